@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark: 1080p multi-scale TTC/FOE frame pairs per second on GB300.
+
+One step = the whole hot path over one synthetic video: 300 uint8 1920x1080 frames
+of a textured plane tilted 20 degrees (camera within 15 degrees of the optical axis,
+Z0 = 20, 0.05 per frame), 5-level pyramid, 2x2x2 derivatives, G, the ten sums, FP64
+merge and 3x3 FOE solve for all 299 consecutive pairs (two launches: the fused tile
+kernel and the merge/solve kernel).  The 622 MB video is larger than L2 (129 MB),
+so no flush is needed between steps.
+
+Also reported in the same JSON line:
+  roofline     of the fused tile kernel (CUDA events on its stream, timed region)
+  e2e          the same metric through the public API with pinned host frames
+               (H2D copy of the video and D2H of the results inside the timed region)
+  cpu_baseline the FP64 oracle on a bounded sample of the same video, one core
+  fastconv     the FastConv sweep (1080x1920 with k x k Gaussians, 64x256x256 with k^3)
+               in GB/s and fraction of the measured HBM peak, L2 flushed between runs
+  accuracy     TTC/FOE mean squared error against ground truth per level and per
+               multi-scale rule (Sec. V-B)
+  clocks       nvidia-smi samples taken during the timed region
+
+``--impl reference`` times the FP64 oracle (the only reference that exists for this
+method) on a bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "1080p multi-scale TTC frame-pairs/s; conv HBM GB/s % of peak; serve p50/p99 ms"
+UNIT = "frame-pairs/s"
+H, W, T_FRAMES, LEVELS = 1080, 1920, 300, 5
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+def _config(frames):
+    return {"workload": f"ttc_video_1080p_{frames}frames_{LEVELS}levels_foe",
+            "H": H, "W": W, "frames": frames, "pairs_per_step": frames - 1, "levels": LEVELS,
+            "mode": "foe", "frame_dtype": "u8",
+            "l2": "inputs 622 MB per step > 129 MB L2 (no flush needed)"}
+
+
+# --------------------------------------------------------------------------- #
+# clocks
+# --------------------------------------------------------------------------- #
+
+def _smi_index(local: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local < len(ids):
+            return ids[local]
+    return str(local)
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.proc = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- #
+# reference arm: the FP64 oracle on the host
+# --------------------------------------------------------------------------- #
+
+def run_reference(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import scenes
+    oracle.build()
+    sc = scenes.tilted_plane_scene(H=H, W=W, seed=args.seed)
+    pairs_per_step = args.ref_pairs
+    fr = scenes.render_sequence(sc, pairs_per_step + 1).numpy()
+    for _ in range(args.warmup):
+        oracle.ttc_pair(fr[0], fr[1], levels=LEVELS, mode=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for t in range(pairs_per_step):
+            oracle.ttc_pair(fr[t], fr[t + 1], levels=LEVELS, mode=1)
+    dt = time.perf_counter() - t0
+    value = pairs_per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(_config(T_FRAMES), sample=f"{pairs_per_step} pairs of the video per step"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{pairs_per_step} 1080p pairs x {args.steps} steps, 5 levels, FOE"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- #
+# our arm
+# --------------------------------------------------------------------------- #
+
+def fastconv_sweep(dev, hbm_peak, reps):
+    import torch
+    import paper_1612_08825_gb300 as ft
+    import scenes
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    cases = [((1080, 1920), (k, k), "gauss") for k in (2, 3, 7, 15)] + \
+            [((64, 256, 256), (k, k, k), "normal") for k in (2, 5)]
+    launches = 0
+    for shape, kshape, kind in cases:
+        E = torch.from_numpy(scenes.uniform_array(shape, seed=2024)).to(dev)
+        if kind == "gauss":
+            k = torch.from_numpy(scenes.gaussian_kernel(kshape[0])).to(dev)
+        else:
+            k = torch.from_numpy(scenes.normal_array(kshape, seed=78)).to(dev)
+        out = ft.fastconv_nd(E, k)
+        s = torch.cuda.current_stream(dev)
+        times = []
+        for i in range(reps + 2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            ft.fastconv_nd(E, k, out=out)
+            e1.record(s)
+            launches += 1
+            times.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        ms = [a.elapsed_time(b) for a, b in times[2:]]
+        t = float(np.median(ms)) * 1e-3
+        nE, nk, no = E.numel(), k.numel(), out.numel()
+        byts = 4 * (nE + no + nk)
+        flops = 2.0 * nE * nk
+        gbs = byts / t / 1e9
+        rows.append({"input": list(shape), "kernel": list(kshape), "us": t * 1e6,
+                     "GBps": gbs, "hbm_frac": gbs / hbm_peak, "GFLOPps": flops / t / 1e9,
+                     "algorithmic_bytes": byts, "flops": flops})
+    del flush
+    return rows, launches
+
+
+def accuracy(sc, res, levels):
+    import paper_1612_08825_gb300 as ft
+    import scenes
+    npairs = res.shape[0]
+    gt = np.array([scenes.ground_truth(sc, t + 0.5) for t in range(npairs)])
+    out = {"ttc_mse_per_level": [], "foe_mse_px2_per_level": []}
+    for l in range(levels):
+        r = res[:, l]
+        out["ttc_mse_per_level"].append(float(np.mean((r["ttc"] - gt[:, 0]) ** 2)))
+        out["foe_mse_px2_per_level"].append(float(np.mean((r["x0"] - gt[:, 1]) ** 2 + (r["y0"] - gt[:, 2]) ** 2)))
+    for rule in (0, 1):
+        chosen = np.array([ft.select_level(res[t], rule) for t in range(npairs)])
+        ttc = np.array([res[t, c]["ttc"] if c >= 0 else np.nan for t, c in enumerate(chosen)])
+        foe = np.array([(res[t, c]["x0"], res[t, c]["y0"]) if c >= 0 else (np.nan, np.nan)
+                        for t, c in enumerate(chosen)])
+        out[f"ttc_mse_rule{rule}"] = float(np.nanmean((ttc - gt[:, 0]) ** 2))
+        out[f"foe_mse_px2_rule{rule}"] = float(np.nanmean((foe[:, 0] - gt[:, 1]) ** 2 + (foe[:, 1] - gt[:, 2]) ** 2))
+        out[f"levels_chosen_rule{rule}"] = np.bincount(chosen[chosen >= 0], minlength=levels).tolist()
+    out["ttc_gt_range"] = [float(gt[:, 0].min()), float(gt[:, 0].max())]
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1612_08825_gb300 as ft
+    import scenes
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ft.load()
+    hbm_peak, sm_max, peak_src = _peaks()
+
+    frames_n = args.frames
+    npairs = frames_n - 1
+    # every rank works on its own video (independent pairs: weak scaling)
+    sc = scenes.tilted_plane_scene(H=H, W=W, seed=args.seed + rank)
+    frames = scenes.render_sequence(sc, frames_n, device=dev)
+    ctx = ft.TtcContext(H, W, LEVELS, npairs, device=dev)
+    out = ctx.new_results(npairs * LEVELS)
+    s = torch.cuda.current_stream(dev)
+
+    def step(evs=None):
+        if evs is not None:
+            evs[0].record(s)
+        ctx.partial_sums(frames, levels=LEVELS)
+        if evs is not None:
+            evs[1].record(s)
+        ctx.reduce_solve(out, mode=ft.MODE_FOE)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    clocks = ClockSampler(_smi_index(local))
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(s)
+    for i in range(args.steps):
+        step(ev[i])
+    end.record(s)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    elapsed = start.elapsed_time(end) * 1e-3
+    tile_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    t_all = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    tmax = float(t_all.item())
+    value = npairs * args.steps * world / tmax
+
+    res = ft.results_to_numpy(out).reshape(npairs, LEVELS)
+
+    # parity spot check of the timed results against the oracle (rank 0, two pairs)
+    parity = None
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        host = frames[: min(frames_n, args.cpu_pairs + 1)].cpu().numpy()
+        worst = 0.0
+        t0 = time.perf_counter()
+        n_done = 0
+        for t in range(min(args.cpu_pairs, host.shape[0] - 1)):
+            ref = oracle.ttc_pair(host[t], host[t + 1], levels=LEVELS, mode=1)
+            n_done += 1
+            for l in range(LEVELS):
+                err = np.abs(res[t, l]["sums"] - ref[l]["sums"]) / np.maximum(ref[l]["abssums"], 1e-300)
+                worst = max(worst, float(err.max()))
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        dt_cpu = time.perf_counter() - t0
+        cpu = {"value": n_done / dt_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {n_done} pairs of the same video, 5 levels, FOE, single thread"}
+        parity = {"pairs_checked": n_done, "max_sum_err_rel_abssum": worst, "tolerance": 1e-5}
+
+    # e2e through the public API with pinned host frames
+    e2e = None
+    if not args.no_e2e:
+        host_frames = frames.cpu().pin_memory()
+        hout = torch.empty(npairs * LEVELS * ft.RESULT_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+        for _ in range(2):
+            ctx.solve_sequence(host_frames, levels=LEVELS, mode=ft.MODE_FOE, out=hout)
+        torch.cuda.synchronize(dev)
+        k2 = max(2, args.steps // 2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(s)
+        for _ in range(k2):
+            ctx.solve_sequence(host_frames, levels=LEVELS, mode=ft.MODE_FOE, out=hout)
+        e1.record(s)
+        torch.cuda.synchronize(dev)
+        te = torch.tensor([e0.elapsed_time(e1) * 1e-3], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": npairs * k2 * world / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(host_frames.numel()), "d2h_bytes_per_step": int(hout.numel())}
+        e2e_res = ft.results_to_numpy(hout).reshape(npairs, LEVELS)
+        assert e2e_res.tobytes() == res.tobytes(), "host-buffer path disagrees with device path"
+
+    conv_rows, conv_launches = (None, 0)
+    if rank == 0 and not args.no_conv:
+        conv_rows, conv_launches = fastconv_sweep(dev, hbm_peak, reps=args.conv_reps)
+
+    if rank == 0:
+        algo_bytes = frames_n * H * W + npairs * LEVELS * 72 * 10 * 4
+        achieved = algo_bytes / (tile_ms * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": _config(frames_n),
+            "roofline": {"kernel": "ttc_tile_kernel<u8>", "bound": "hbm", "achieved": achieved,
+                         "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": None, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": tile_ms},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": ck,
+            "parity": parity,
+            "accuracy": accuracy(sc, res, LEVELS),
+            "fastconv": conv_rows,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=T_FRAMES)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-pairs", type=int, default=120)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-pairs", type=int, default=8)
+    ap.add_argument("--conv-reps", type=int, default=20)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-conv", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

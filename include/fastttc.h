@@ -1,0 +1,200 @@
+/*
+ * fastttc.h - C ABI of the GB300 (sm_103a) FastConv and time-to-contact library.
+ *
+ * Paper: "Accelerated Convolutions for Efficient Multi-Scale Time to Contact
+ * Computation in Julia" (Amini, Horn, Edelman).
+ *
+ * General conventions
+ *  - Every entry point returns an ft_status (or a plain int where stated).  No C++
+ *    exception and no abort ever crosses this boundary.
+ *  - All arguments are validated on the host before anything is launched; an
+ *    invalid call launches nothing and leaves every output untouched.
+ *  - Pointers named "device" must point to memory of the current CUDA device; the
+ *    caller owns every buffer passed in.  The library allocates device memory only
+ *    in ttc_ctx_create (freed by ttc_ctx_destroy); no other call allocates.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device work is enqueued asynchronously on it; no call synchronises
+ *    the device.  Results are valid once the stream has reached the call.
+ *  - A CUDA launch failure is reported as FT_ERR_CUDA (the CUDA error string is
+ *    available from ft_last_cuda_error()).
+ *  - Arrays are row-major (C order, last dimension fastest).
+ */
+#ifndef FASTTTC_H
+#define FASTTTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FT_OK = 0,
+    FT_ERR_INVALID_ARG = 1,   /* null pointer, bad enum value, negative size */
+    FT_ERR_SHAPE = 2,         /* dimensions inconsistent or too small for the request */
+    FT_ERR_UNSUPPORTED = 3,   /* valid request beyond this build's limits */
+    FT_ERR_WORKSPACE = 4,     /* request larger than the context was created for */
+    FT_ERR_CUDA = 5           /* a CUDA runtime call failed */
+} ft_status;
+
+#define FT_MAX_NDIM 8         /* fastconv_nd: largest rank */
+#define FT_MAX_LEVELS 7       /* ttc_*: largest number of pyramid levels */
+
+/* Human-readable name of a status code (static string). */
+const char *ft_status_string(int status);
+/* Text of the last CUDA error seen by this library in the calling thread, or "". */
+const char *ft_last_cuda_error(void);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int ft_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* FastConv: direct n-dimensional full convolution (Sec. IV-C, Eq. conv2)    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Output extent of the full convolution (Sec. IV: the operation FastConv replaces
+ * is the full linear convolution): out_dims[d] = dims[d] + kdims[d] - 1.
+ * Host only.  dims, kdims: nd host int64 values, each >= 1; out_dims: nd values
+ * written on success.  Errors: FT_ERR_INVALID_ARG (null), FT_ERR_SHAPE (nd outside
+ * [1, FT_MAX_NDIM] or an extent < 1).
+ */
+ft_status fastconv_out_dims(int nd, const int64_t *dims, const int64_t *kdims, int64_t *out_dims);
+
+/*
+ * Full n-D convolution, FP32 (Eq. conv2 read as the full linear convolution):
+ *     out[p] = sum over r of kernel[r] * input[p - r],
+ * over every kernel index r with p - r inside the input (zero outside).
+ *   input  : device, prod(dims) floats, row-major contiguous.
+ *   dims   : host, nd extents (each >= 1).
+ *   kernel : device, prod(kdims) floats, row-major contiguous.
+ *   kdims  : host, nd extents (each >= 1).  A kernel larger than the input is allowed.
+ *   out    : device, prod(dims + kdims - 1) floats; every element is written.
+ *   nd     : rank, 1 <= nd <= FT_MAX_NDIM.
+ * Accumulation is FP32 in a fixed order.  input/kernel must not overlap out.
+ * Errors: FT_ERR_INVALID_ARG, FT_ERR_SHAPE, FT_ERR_UNSUPPORTED (output or kernel
+ * with more than 2^62 elements), FT_ERR_CUDA.
+ */
+ft_status fastconv_nd(const float *input, const int64_t *dims, int nd,
+                      const float *kernel, const int64_t *kdims, float *out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Time to contact (Sec. V-A, V-B)                                           */
+/* ------------------------------------------------------------------------ */
+
+typedef enum { FT_U8 = 0, FT_F32 = 1 } ft_dtype;   /* frame pixel type */
+typedef enum { FT_MODE_TTC = 0, FT_MODE_FOE = 1 } ft_mode;
+
+/* Per-result flags (information, not errors). */
+#define FT_FLAG_SINGULAR 1   /* normal equations singular: A, B, C, TTC, FOE are NaN */
+#define FT_FLAG_C_ZERO 2     /* C == 0: TTC = +inf, FOE = NaN */
+#define FT_FLAG_RECEDING 4   /* C < 0: the camera moves away; TTC is negative */
+
+/*
+ * One solve result for one frame pair at one pyramid level (152 bytes).
+ *  sums : the ten least-squares sums of Sec. V-A over all 2x2x2 cubes of the
+ *         level, in the units of the level-l image (block means of the input
+ *         brightness) and level-l pixels, in this order:
+ *         0 Ex^2, 1 Ex Ey, 2 Ey^2, 3 G Ex, 4 G Ey, 5 G^2, 6 Ex Et, 7 Ey Et, 8 G Et, 9 Et^2.
+ *  A, B, C : solution of the normal equations (mode FT_MODE_TTC: A = B = 0).
+ *  ttc  : 1/C in frame intervals (Eq. final_TTC).
+ *  x0, y0 : focus of expansion -A/C, -B/C, converted to level-0 pixels, measured
+ *         from the image centre ((W-1)/2, (H-1)/2), x right, y down.
+ *  resid : sum over cubes of (A Ex + B Ey + C G + Et)^2 divided by sum Et^2.
+ *  n    : number of cubes summed, (H_l - 1) (W_l - 1).
+ */
+typedef struct {
+    double sums[10];
+    double A, B, C;
+    double ttc, x0, y0;
+    double resid;
+    int64_t n;
+    int32_t level;
+    int32_t flags;
+} ttc_level_result;
+
+/*
+ * The 2x2x2 derivative estimates of Sec. II / V-A at level 0, materialised.
+ * For the cube with corner (i, j) (rows i, i+1; columns j, j+1; frames prev, cur):
+ *   Ex = mean of the four x first differences, Ey = mean of the four y first
+ *   differences, Et = mean of the four t first differences (cur - prev),
+ *   G  = x Ex + y Ey with x = j + 1/2 - (W-1)/2, y = i + 1/2 - (H-1)/2.
+ *   prev, cur : device, H rows of W pixels of `dtype`, row stride pitch_bytes.
+ *   Ex, Ey, Et : device, (H-1) x (W-1) floats each, contiguous.
+ *   G : device, (H-1) x (W-1) floats, or NULL to skip it.
+ * For FT_U8 frames Ex, Ey and Et are exact (integer sums / 4).
+ * Errors: FT_ERR_INVALID_ARG, FT_ERR_SHAPE (H or W < 2, pitch_bytes < W * pixel
+ * size or not a multiple of the pixel size), FT_ERR_CUDA.
+ */
+ft_status ttc_derivatives(const void *prev, const void *cur, int dtype, int H, int W,
+                          int64_t pitch_bytes, float *Ex, float *Ey, float *Et, float *G,
+                          void *stream);
+
+/*
+ * A context owns the device workspace for the per-tile partial sums (allocated
+ * here, once) for requests up to max_H x max_W frames, max_levels levels and
+ * max_pairs frame pairs per call.  One context must not be used by two host
+ * threads at once; different contexts are independent.
+ * Errors: FT_ERR_INVALID_ARG, FT_ERR_SHAPE, FT_ERR_CUDA (allocation failed).
+ */
+typedef struct ttc_ctx ttc_ctx;
+ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max_levels, int max_pairs);
+void ttc_ctx_destroy(ttc_ctx *ctx);
+/* Bytes of device workspace the context holds. */
+size_t ttc_ctx_workspace_bytes(const ttc_ctx *ctx);
+
+/*
+ * Multi-scale TTC/FOE for one frame pair (Sec. V-A, V-B): for each level
+ * l = 0 .. levels-1, the level-l images are the l-fold 2x2 block means of prev and
+ * cur (floor cropping: H_l = floor(H / 2^l)); the ten sums are taken over all
+ * (H_l - 1)(W_l - 1) cubes of level l with x, y measured from the level-0 image
+ * centre expressed in level-l pixels, (W - 2^l) / 2^(l+1) and (H - 2^l) / 2^(l+1);
+ * then the 3x3 normal equations (mode FT_MODE_FOE) or the TTC-only equation
+ * (FT_MODE_TTC: C = -sum(G Et) / sum(G^2)) are solved in FP64.
+ *   prev, cur : device frames, H x W pixels of `dtype`, row stride pitch_bytes.
+ *   out : device, `levels` results, out[l] for level l.
+ * Per-cube products are formed in FP32 and summed pairwise in FP32 within each
+ * tile; tiles are merged in FP64 in a fixed order (results are deterministic).
+ * Errors: FT_ERR_INVALID_ARG, FT_ERR_SHAPE (a level smaller than 2 x 2, pitch),
+ * FT_ERR_UNSUPPORTED (levels > FT_MAX_LEVELS), FT_ERR_WORKSPACE (request larger
+ * than the context), FT_ERR_CUDA.
+ */
+ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, int dtype, int H, int W,
+                    int64_t pitch_bytes, int levels, int mode, ttc_level_result *out,
+                    void *stream);
+
+/*
+ * The same for the T-1 consecutive pairs (t, t+1) of a video of T frames stored
+ * frame_stride_bytes apart: out[(t * levels) + l] for pair t, level l (device,
+ * (T-1) * levels results).  Sec. V-B: the estimate is produced at every frame.
+ */
+ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
+                             int dtype, int H, int W, int64_t pitch_bytes, int levels, int mode,
+                             ttc_level_result *out, void *stream);
+
+/*
+ * The two stages of ttc_solve_sequence, for callers that time or overlap them.
+ * ttc_partial_sums runs the fused pyramid + stencil + G + product + tile-reduction
+ * kernel and leaves FP32 per-tile partial sums in the context; ttc_reduce_solve
+ * merges them in FP64 and solves.  ttc_reduce_solve uses the geometry of the last
+ * ttc_partial_sums call on the same context and must follow it on the same stream.
+ */
+ft_status ttc_partial_sums(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
+                           int dtype, int H, int W, int64_t pitch_bytes, int levels, void *stream);
+ft_status ttc_reduce_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, void *stream);
+
+/*
+ * Multi-scale selection (Sec. V-B), host only: start at the finest usable level
+ * and move one level coarser while the next level is usable and its key is
+ * smaller ("improved (ie. reduced)"); rule 0: key = TTC; rule 1: key = resid.
+ * A level is usable when flags has neither FT_FLAG_SINGULAR nor FT_FLAG_C_ZERO
+ * and TTC > 0.  host_results: `levels` results of one pair, level order.
+ * Returns the chosen level, -1 if no level is usable, -2 on invalid arguments.
+ */
+int ttc_select_level(const ttc_level_result *host_results, int levels, int rule);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTTTC_H */

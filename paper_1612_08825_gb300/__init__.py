@@ -1,0 +1,312 @@
+"""GB300 (sm_103a) FastConv and multi-scale time-to-contact, Python binding.
+
+Paper: "Accelerated Convolutions for Efficient Multi-Scale Time to Contact
+Computation in Julia" (Amini, Horn, Edelman).
+
+This module only marshals arguments to the C ABI of ``libfastttc.so`` (declared in
+``include/fastttc.h``): torch tensors supply device memory and the current CUDA
+stream; every step of the computation runs in the library's CUDA kernels.  There
+is no CPU fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "ttc_derivatives",
+    "TtcContext", "RESULT_DTYPE", "results_to_numpy", "select_level",
+    "MODE_TTC", "MODE_FOE", "FLAG_SINGULAR", "FLAG_C_ZERO", "FLAG_RECEDING", "MAX_LEVELS",
+    "MAX_NDIM",
+]
+
+MODE_TTC, MODE_FOE = 0, 1
+DTYPE_U8, DTYPE_F32 = 0, 1
+FLAG_SINGULAR, FLAG_C_ZERO, FLAG_RECEDING = 1, 2, 4
+MAX_LEVELS = 7
+MAX_NDIM = 8
+
+# mirror of ttc_level_result (152 bytes)
+RESULT_DTYPE = np.dtype([
+    ("sums", np.float64, (10,)),
+    ("A", np.float64), ("B", np.float64), ("C", np.float64),
+    ("ttc", np.float64), ("x0", np.float64), ("y0", np.float64),
+    ("resid", np.float64),
+    ("n", np.int64),
+    ("level", np.int32), ("flags", np.int32),
+])
+assert RESULT_DTYPE.itemsize == 152
+
+_lib = None
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+
+
+class FtError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        name = _lib.ft_status_string(status).decode() if _lib is not None else str(status)
+        extra = ""
+        if _lib is not None and status == 5:
+            extra = ": " + _lib.ft_last_cuda_error().decode()
+        super().__init__(f"{what} failed with {name}{extra}")
+        self.status = status
+
+
+def load(path: Optional[str] = None):
+    """Load libfastttc.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    st = ctypes.c_int
+    L.ft_status_string.argtypes = [ctypes.c_int]
+    L.ft_status_string.restype = ctypes.c_char_p
+    L.ft_last_cuda_error.argtypes = []
+    L.ft_last_cuda_error.restype = ctypes.c_char_p
+    L.ft_version.restype = ctypes.c_int
+    L.fastconv_out_dims.argtypes = [ctypes.c_int, _i64p, _i64p, _i64p]
+    L.fastconv_out_dims.restype = st
+    L.fastconv_nd.argtypes = [_vp, _i64p, ctypes.c_int, _vp, _i64p, _vp, _vp]
+    L.fastconv_nd.restype = st
+    L.ttc_derivatives.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                  _vp, _vp, _vp, _vp, _vp]
+    L.ttc_derivatives.restype = st
+    L.ttc_ctx_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.ttc_ctx_create.restype = st
+    L.ttc_ctx_destroy.argtypes = [_vp]
+    L.ttc_ctx_destroy.restype = None
+    L.ttc_ctx_workspace_bytes.argtypes = [_vp]
+    L.ttc_ctx_workspace_bytes.restype = ctypes.c_size_t
+    L.ttc_solve.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                            ctypes.c_int, ctypes.c_int, _vp, _vp]
+    L.ttc_solve.restype = st
+    L.ttc_solve_sequence.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _vp, _vp]
+    L.ttc_solve_sequence.restype = st
+    L.ttc_partial_sums.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int64, ctypes.c_int, _vp]
+    L.ttc_partial_sums.restype = st
+    L.ttc_reduce_solve.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+    L.ttc_reduce_solve.restype = st
+    L.ttc_select_level.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    L.ttc_select_level.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def lib():
+    return load()
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise FtError(status, what)
+
+
+def _stream_ptr(t: torch.Tensor) -> int:
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def _require_cuda(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+
+
+def _dims(seq: Sequence[int]):
+    arr = (ctypes.c_int64 * len(seq))(*[int(v) for v in seq])
+    return arr
+
+
+# --------------------------------------------------------------------------- #
+# FastConv
+# --------------------------------------------------------------------------- #
+
+def fastconv_out_dims(dims: Sequence[int], kdims: Sequence[int]) -> tuple:
+    """Full-convolution output extent (host call into the library)."""
+    L = load()
+    nd = len(dims)
+    if len(kdims) != nd:
+        raise ValueError("dims and kdims must have the same length")
+    out = (ctypes.c_int64 * max(nd, 1))()
+    _check(L.fastconv_out_dims(nd, _dims(dims), _dims(kdims), out), "fastconv_out_dims")
+    return tuple(int(out[i]) for i in range(nd))
+
+
+def fastconv_nd(x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Full n-D convolution of x with k (FP32, Eq. conv2 read as the full linear convolution)."""
+    L = load()
+    _require_cuda(x, "x")
+    _require_cuda(k, "k")
+    if x.dtype != torch.float32 or k.dtype != torch.float32:
+        raise ValueError("fastconv_nd takes float32 tensors")
+    if x.dim() != k.dim():
+        raise ValueError("x and k must have the same rank")
+    x = x.contiguous()
+    k = k.contiguous()
+    od = fastconv_out_dims(x.shape, k.shape)
+    if out is None:
+        out = torch.empty(od, dtype=torch.float32, device=x.device)
+    elif tuple(out.shape) != od or not out.is_contiguous() or out.dtype != torch.float32:
+        raise ValueError("out has the wrong shape, dtype or layout")
+    _check(L.fastconv_nd(x.data_ptr(), _dims(x.shape), x.dim(), k.data_ptr(), _dims(k.shape),
+                         out.data_ptr(), _stream_ptr(x)), "fastconv_nd")
+    return out
+
+
+# --------------------------------------------------------------------------- #
+# Time to contact
+# --------------------------------------------------------------------------- #
+
+def _frame_args(t: torch.Tensor):
+    if t.dtype == torch.uint8:
+        return DTYPE_U8, 1
+    if t.dtype == torch.float32:
+        return DTYPE_F32, 4
+    raise ValueError("frames must be uint8 or float32")
+
+
+def ttc_derivatives(prev: torch.Tensor, cur: torch.Tensor, with_G: bool = True):
+    """Level-0 Ex, Ey, Et (and G), each (H-1, W-1) float32."""
+    L = load()
+    _require_cuda(prev, "prev")
+    _require_cuda(cur, "cur")
+    if prev.shape != cur.shape or prev.dtype != cur.dtype or prev.dim() != 2:
+        raise ValueError("prev and cur must be 2-D tensors of one shape and dtype")
+    if prev.stride(1) != 1 or cur.stride(1) != 1 or prev.stride(0) != cur.stride(0):
+        raise ValueError("rows must be contiguous with one common pitch")
+    dt, es = _frame_args(prev)
+    H, W = prev.shape
+    outs = [torch.empty((max(H - 1, 0), max(W - 1, 0)), dtype=torch.float32, device=prev.device)
+            for _ in range(4 if with_G else 3)]
+    G = outs[3].data_ptr() if with_G else None
+    _check(L.ttc_derivatives(prev.data_ptr(), cur.data_ptr(), dt, H, W, prev.stride(0) * es,
+                             outs[0].data_ptr(), outs[1].data_ptr(), outs[2].data_ptr(), G,
+                             _stream_ptr(prev)), "ttc_derivatives")
+    return tuple(outs)
+
+
+def results_to_numpy(t: torch.Tensor) -> np.ndarray:
+    """Device/host byte tensor of ttc_level_result records -> numpy structured array."""
+    a = t.detach().to("cpu").contiguous().numpy()
+    return a.view(RESULT_DTYPE).reshape(-1)
+
+
+def select_level(results: np.ndarray, rule: int = 0) -> int:
+    """Multi-scale selection (Sec. V-B) over one pair's per-level results (host)."""
+    L = load()
+    r = np.ascontiguousarray(results, dtype=RESULT_DTYPE)
+    v = L.ttc_select_level(r.ctypes.data, r.shape[0], int(rule))
+    if v == -2:
+        raise ValueError("invalid arguments to ttc_select_level")
+    return int(v)
+
+
+class TtcContext:
+    """Owns the library's partial-sum workspace (ttc_ctx) for requests up to a size."""
+
+    def __init__(self, max_H: int, max_W: int, max_levels: int = 5, max_pairs: int = 1,
+                 device: Optional[torch.device] = None):
+        L = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.max = (max_H, max_W, max_levels, max_pairs)
+        h = _vp()
+        with torch.cuda.device(self.device):
+            _check(L.ttc_ctx_create(ctypes.byref(h), max_H, max_W, max_levels, max_pairs), "ttc_ctx_create")
+        self._h = h
+        self._staging = None
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(load().ttc_ctx_workspace_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ttc_ctx_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_results(self, n: int) -> torch.Tensor:
+        return torch.empty(n * RESULT_DTYPE.itemsize, dtype=torch.uint8, device=self.device)
+
+    def solve(self, prev: torch.Tensor, cur: torch.Tensor, levels: int = 1, mode: int = MODE_FOE,
+              out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """One frame pair -> byte tensor of `levels` ttc_level_result records (device)."""
+        L = load()
+        _require_cuda(prev, "prev")
+        _require_cuda(cur, "cur")
+        if prev.shape != cur.shape or prev.dtype != cur.dtype or prev.dim() != 2:
+            raise ValueError("prev and cur must be 2-D tensors of one shape and dtype")
+        if prev.stride(1) != 1 or cur.stride(1) != 1 or prev.stride(0) != cur.stride(0):
+            raise ValueError("rows must be contiguous with one common pitch")
+        dt, es = _frame_args(prev)
+        H, W = prev.shape
+        out = self.new_results(levels) if out is None else out
+        _check(L.ttc_solve(self._h, prev.data_ptr(), cur.data_ptr(), dt, H, W, prev.stride(0) * es,
+                           int(levels), int(mode), out.data_ptr(), _stream_ptr(prev)), "ttc_solve")
+        return out
+
+    def _seq_args(self, frames: torch.Tensor):
+        if frames.dim() != 3 or frames.stride(2) != 1:
+            raise ValueError("frames must be (T, H, W) with contiguous rows")
+        dt, es = _frame_args(frames)
+        T, H, W = frames.shape
+        return dt, es, T, H, W
+
+    def solve_sequence(self, frames: torch.Tensor, levels: int = 1, mode: int = MODE_FOE,
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """T frames -> (T-1) * levels records.
+
+        With CUDA frames the records stay on the device (asynchronous).  With host
+        frames (ideally pinned) the frames are copied to the device, solved, and the
+        records are copied back to a host tensor, all on the current stream.
+        """
+        L = load()
+        host = not frames.is_cuda
+        if host:
+            if self._staging is None or self._staging.shape != frames.shape or self._staging.dtype != frames.dtype:
+                self._staging = torch.empty(frames.shape, dtype=frames.dtype, device=self.device)
+            self._staging.copy_(frames, non_blocking=True)
+            dev_frames = self._staging
+        else:
+            dev_frames = frames
+        dt, es, T, H, W = self._seq_args(dev_frames)
+        n = (T - 1) * levels
+        dev_out = self.new_results(n) if (out is None or host) else out
+        _check(L.ttc_solve_sequence(self._h, dev_frames.data_ptr(), dev_frames.stride(0) * es, T, dt, H, W,
+                                    dev_frames.stride(1) * es, int(levels), int(mode), dev_out.data_ptr(),
+                                    _stream_ptr(dev_frames)), "ttc_solve_sequence")
+        if host:
+            host_out = out if out is not None else torch.empty(n * RESULT_DTYPE.itemsize, dtype=torch.uint8,
+                                                                pin_memory=True)
+            host_out.copy_(dev_out, non_blocking=True)
+            return host_out
+        return dev_out
+
+    def partial_sums(self, frames: torch.Tensor, levels: int = 1):
+        """Stage 1 only (fused pyramid/stencil/products/tile reduction)."""
+        L = load()
+        _require_cuda(frames, "frames")
+        dt, es, T, H, W = self._seq_args(frames)
+        _check(L.ttc_partial_sums(self._h, frames.data_ptr(), frames.stride(0) * es, T, dt, H, W,
+                                  frames.stride(1) * es, int(levels), _stream_ptr(frames)), "ttc_partial_sums")
+
+    def reduce_solve(self, out: torch.Tensor, mode: int = MODE_FOE):
+        """Stage 2 only (FP64 merge + solve) for the last partial_sums call."""
+        L = load()
+        _check(L.ttc_reduce_solve(self._h, int(mode), out.data_ptr(), _stream_ptr(out)), "ttc_reduce_solve")
+        return out

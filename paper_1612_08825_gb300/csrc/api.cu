@@ -1,0 +1,34 @@
+// Status strings, version and CUDA-error bookkeeping of the fastttc C ABI.
+#include <cstring>
+
+#include "common.cuh"
+
+namespace ft {
+
+static thread_local char g_cuda_error[256] = "";
+
+void set_cuda_error(cudaError_t e)
+{
+    const char *s = cudaGetErrorString(e);
+    std::strncpy(g_cuda_error, s ? s : "unknown CUDA error", sizeof(g_cuda_error) - 1);
+    g_cuda_error[sizeof(g_cuda_error) - 1] = '\0';
+}
+
+}  // namespace ft
+
+extern "C" const char *ft_status_string(int status)
+{
+    switch (status) {
+    case FT_OK: return "FT_OK";
+    case FT_ERR_INVALID_ARG: return "FT_ERR_INVALID_ARG";
+    case FT_ERR_SHAPE: return "FT_ERR_SHAPE";
+    case FT_ERR_UNSUPPORTED: return "FT_ERR_UNSUPPORTED";
+    case FT_ERR_WORKSPACE: return "FT_ERR_WORKSPACE";
+    case FT_ERR_CUDA: return "FT_ERR_CUDA";
+    default: return "FT_ERR_UNKNOWN";
+    }
+}
+
+extern "C" const char *ft_last_cuda_error(void) { return ft::g_cuda_error; }
+
+extern "C" int ft_version(void) { return 1 * 10000 + 0 * 100 + 0; }

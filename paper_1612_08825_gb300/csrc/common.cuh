@@ -1,0 +1,29 @@
+// Shared host/device helpers of the fastttc CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fastttc.h"
+
+namespace ft {
+
+// Records the text of a CUDA error for ft_last_cuda_error() (thread-local).
+void set_cuda_error(cudaError_t e);
+
+// FT_OK if the last launch on this thread succeeded, else FT_ERR_CUDA.
+inline ft_status check_launch()
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    return FT_OK;
+}
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace ft

@@ -1,0 +1,139 @@
+"""Host-side checks of the C ABI that need no GPU.
+
+The library loads on a machine without a GPU; every function declared in
+include/fastttc.h is exported; argument validation happens on the host before any
+CUDA call; the host-only functions (output dims, status strings, multi-scale
+selection) agree with the oracle and the hand-worked fixtures.
+"""
+import ctypes
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1612_08825_gb300 as ft
+from paper_1612_08825_gb300 import build as ftbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    ftbuild.build_library()
+    return ft.load()
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            prefix = text[:m.start()].rstrip()
+            if name in ("if", "while", "sizeof", "defined") or prefix.endswith("#define"):
+                continue
+            # a declaration: preceded by a type token at statement start
+            line_start = text.rfind(";", 0, m.start())
+            stmt = text[line_start + 1:m.start()]
+            if "typedef" in stmt or "#" in stmt.split("\n")[-1]:
+                continue
+            if re.search(r"[A-Za-z_]", stmt):
+                names.add(name)
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared_functions()
+    assert {"fastconv_nd", "fastconv_out_dims", "ttc_derivatives", "ttc_solve",
+            "ttc_solve_sequence", "ttc_select_level", "ttc_ctx_create"} <= names
+    for n in sorted(names):
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+
+
+def test_status_strings_and_version(L):
+    assert L.ft_status_string(0) == b"FT_OK"
+    assert L.ft_status_string(2) == b"FT_ERR_SHAPE"
+    assert L.ft_status_string(99) == b"FT_ERR_UNKNOWN"
+    assert L.ft_version() >= 10000
+
+
+def test_out_dims(L):
+    assert ft.fastconv_out_dims((1080, 1920), (3, 3)) == (1082, 1922)
+    assert ft.fastconv_out_dims((64, 256, 256), (5, 5, 5)) == (68, 260, 260)
+    assert ft.fastconv_out_dims((2, 3), (5, 4)) == (6, 6)
+    for dims, kd in [((1080, 1920), (2, 2)), ((7,), (11,)), ((1, 2, 3, 4, 5, 6, 7, 8), (2,) * 8)]:
+        assert ft.fastconv_out_dims(dims, kd) == oracle.conv_out_dims(dims, kd)
+    with pytest.raises(ft.FtError):
+        ft.fastconv_out_dims((0, 4), (1, 1))
+    with pytest.raises(ft.FtError):
+        ft.fastconv_out_dims((2,) * 9, (1,) * 9)
+
+
+def test_fastconv_validation_before_launch(L):
+    d = (ctypes.c_int64 * 2)(4, 4)
+    k = (ctypes.c_int64 * 2)(3, 3)
+    bad = (ctypes.c_int64 * 2)(4, 0)
+    # null pointers
+    assert L.fastconv_nd(None, d, 2, 8, k, 8, None) == 1
+    # bad shape with (fake, never dereferenced) pointers: rejected on the host
+    assert L.fastconv_nd(8, bad, 2, 8, k, 8, None) == 2
+    assert L.fastconv_nd(8, d, 0, 8, k, 8, None) == 2
+    assert L.fastconv_nd(8, d, 9, 8, k, 8, None) == 2
+
+
+def test_ttc_validation_before_launch(L):
+    h = ctypes.c_void_p()
+    assert L.ttc_ctx_create(None, 64, 64, 3, 1) == 1
+    assert L.ttc_ctx_create(ctypes.byref(h), 1, 64, 3, 1) == 2
+    assert L.ttc_ctx_create(ctypes.byref(h), 64, 64, 8, 1) == 3
+    assert L.ttc_ctx_create(ctypes.byref(h), 64, 64, 0, 1) == 1
+    # derivatives: bad dtype / shapes / pitch, with fake pointers never dereferenced
+    f = ctypes.c_void_p(16)
+    assert L.ttc_derivatives(f, f, 7, 8, 8, 8, f, f, f, None, None) == 1
+    assert L.ttc_derivatives(f, f, 0, 1, 8, 8, f, f, f, None, None) == 2
+    assert L.ttc_derivatives(f, f, 1, 8, 8, 16, f, f, f, None, None) == 2   # pitch < 4 W
+    assert L.ttc_derivatives(None, f, 0, 8, 8, 8, f, f, f, None, None) == 1
+    assert L.ttc_solve(None, f, f, 0, 8, 8, 8, 1, 1, f, None) == 1
+
+
+def test_select_level_matches_golden_and_oracle(L):
+    with open(os.path.join(ROOT, "tests", "golden", "multiscale_rule.json")) as fh:
+        cases = json.load(fh)["cases"]
+    for case in cases:
+        n = len(case["ttc"])
+        r = np.zeros(n, dtype=ft.RESULT_DTYPE)
+        r["ttc"] = case["ttc"]
+        r["resid"] = case["resid"]
+        r["flags"] = case["flags"]
+        assert ft.select_level(r, 0) == case["rule0"]
+        assert ft.select_level(r, 1) == case["rule1"]
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        n = int(rng.integers(1, 8))
+        r = np.zeros(n, dtype=ft.RESULT_DTYPE)
+        o = np.zeros(n, dtype=oracle.RESULT_DTYPE)
+        ttc = rng.choice([-3.0, 5.0, 10.0, 20.0, 30.0], n)
+        res = rng.choice([0.1, 0.2, 0.3], n)
+        fl = rng.choice([0, 0, 0, 1, 2, 4], n)
+        for a in (r, o):
+            a["ttc"] = ttc
+            a["resid"] = res
+            a["flags"] = fl
+        for rule in (0, 1):
+            assert ft.select_level(r, rule) == oracle.select_level(o, rule)
+    with pytest.raises(ValueError):
+        ft.select_level(np.zeros(2, dtype=ft.RESULT_DTYPE), 3)
+
+
+def test_result_layout_matches_header():
+    text = open(os.path.join(ROOT, "include", "fastttc.h")).read()
+    assert "double sums[10];" in text
+    assert ft.RESULT_DTYPE.itemsize == 152
+    assert ft.RESULT_DTYPE.fields["n"][1] == 136 and ft.RESULT_DTYPE.fields["flags"][1] == 148

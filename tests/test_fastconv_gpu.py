@@ -1,0 +1,143 @@
+"""FastConv (full n-D convolution) through the C ABI vs the FP64 oracle.
+
+Error metric (stated for FP32 with fixed-order accumulation): every element obeys
+    |y - y*| <= 1e-5 * (|E| conv |k|)[p],
+the natural bound for a dot product, relative to the absolute-value convolution
+(a plain relative error is ill-posed where y* ~ 0 for mixed-sign kernels).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1612_08825_gb300 as ft
+import scenes
+
+pytestmark = pytest.mark.gpu
+REL = 1e-5
+
+
+def _run(E: np.ndarray, k: np.ndarray, offset: int = 0) -> np.ndarray:
+    dev = torch.device("cuda")
+    if offset:
+        buf = torch.zeros(E.size + offset, dtype=torch.float32, device=dev)
+        x = buf[offset:].view(E.shape)
+        x.copy_(torch.from_numpy(E))
+    else:
+        x = torch.from_numpy(E).to(dev)
+    out = ft.fastconv_nd(x, torch.from_numpy(k).to(dev))
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _check_full(E, k, offset=0):
+    got = _run(E, k, offset)
+    ref, rabs = oracle.fastconv_nd(E, k, with_abs=True)
+    assert got.shape == ref.shape
+    err = np.abs(got.astype(np.float64) - ref)
+    assert np.all(err <= REL * rabs + 1e-30), float(np.max(err / np.maximum(rabs, 1e-30)))
+    return float(np.max(err / np.maximum(rabs, 1e-30)))
+
+
+@pytest.mark.parametrize("shape,kshape", [
+    ((1,), (1,)), ((17,), (5,)), ((3000,), (31,)), ((5,), (40,)),
+    ((1, 1), (1, 1)), ((7, 9), (3, 3)), ((70, 300), (3, 3)), ((130, 261), (2, 2)),
+    ((99, 257), (7, 7)), ((66, 140), (15, 15)), ((40, 37), (1, 6)), ((33, 50), (9, 1)),
+    ((3, 4), (6, 9)),                        # kernel larger than the input
+    ((5, 37, 45), (2, 3, 4)), ((9, 40, 33), (5, 5, 5)), ((4, 3, 20, 21), (2, 1, 3, 2)),
+    ((2, 2, 2, 2, 2, 2, 3, 5), (2, 1, 2, 1, 2, 1, 2, 3)),   # rank 8
+])
+def test_fastconv_small_shapes(shape, kshape):
+    E = scenes.normal_array(shape, seed=sum(shape))
+    k = scenes.normal_array(kshape, seed=100 + sum(kshape))
+    _check_full(E, k)
+
+
+@pytest.mark.parametrize("kc", [5, 9, 17, 33, 65, 70])
+def test_fastconv_every_padding_bucket_and_direct_fallback(kc):
+    E = scenes.uniform_array((20, 150), seed=kc)
+    k = scenes.normal_array((2, kc), seed=kc + 1)
+    _check_full(E, k)
+
+
+def test_fastconv_unaligned_input_and_odd_width():
+    E = scenes.uniform_array((41, 203), seed=3)
+    k = scenes.normal_array((3, 3), seed=4)
+    _check_full(E, k, offset=1)          # input pointer not 16-byte aligned
+    E = scenes.uniform_array((41, 200), seed=5)
+    _check_full(E, k, offset=1)
+    _check_full(E, k, offset=0)          # aligned, width multiple of 4 (vector path)
+
+
+def test_fastconv_paper_masks_and_delta():
+    # Sec. II derivative mask and Sec. III edge kernels on an image with a vertical edge
+    img = np.zeros((6, 9), np.float32)
+    img[:, 4:] = 1.0
+    kx = np.array([[-0.5, 0.5], [-0.5, 0.5]], np.float32)
+    sobel = np.array([[-1, 0, 1], [-2, 0, 2], [-1, 0, 1]], np.float32)
+    for k in (kx, sobel, kx.T.copy()):
+        got = _run(img, k)
+        np.testing.assert_array_equal(got, oracle.fastconv_nd(img, k).astype(np.float32))
+    E = scenes.normal_array((13, 29), seed=9)
+    d = np.zeros((3, 4), np.float32)
+    d[1, 2] = 1.0
+    got = _run(E, d)
+    np.testing.assert_array_equal(got[1:14, 2:31], E)
+
+
+def test_fastconv_deterministic():
+    E = scenes.uniform_array((300, 500), seed=11)
+    k = scenes.normal_array((7, 7), seed=12)
+    a = _run(E, k)
+    b = _run(E, k)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_fastconv_rejects_empty_and_bad_rank():
+    dev = torch.device("cuda")
+    with pytest.raises(ft.FtError):
+        ft.fastconv_nd(torch.zeros((0, 4), device=dev), torch.ones((1, 1), device=dev))
+    with pytest.raises(ValueError):
+        ft.fastconv_nd(torch.zeros((4, 4), device=dev), torch.ones((1,), device=dev))
+
+
+FULL_2D = [2, 3, 7, 15]
+
+
+@pytest.mark.parametrize("kk", FULL_2D)
+def test_fastconv_full_size_2d_sampled(kk):
+    """1080x1920 U[0,1] conv normalised Gaussian k x k (sigma = k/6), sampled outputs."""
+    E = scenes.uniform_array((1080, 1920), seed=2024)
+    k = scenes.gaussian_kernel(kk)
+    got = _run(E, k)
+    M = got.shape
+    rng = np.random.default_rng(kk)
+    pts = list(rng.integers(0, got.size, 3000))
+    for r in (0, 1, M[0] // 2, M[0] - 2, M[0] - 1):          # borders and ragged edges
+        for c in (0, 1, 127, 128, M[1] // 2, M[1] - 2, M[1] - 1):
+            pts.append(r * M[1] + c)
+    pts = np.array(pts, dtype=np.int64)
+    ref, rabs = oracle.fastconv_points(E, k, pts)
+    g = got.reshape(-1)[pts].astype(np.float64)
+    assert np.all(np.abs(g - ref) <= REL * rabs + 1e-30)
+    # sum identity over the whole output: sum(out) = sum(E) * sum(k)
+    tot = got.astype(np.float64).sum()
+    expect = E.astype(np.float64).sum() * k.astype(np.float64).sum()
+    assert abs(tot - expect) <= REL * abs(expect)
+
+
+@pytest.mark.parametrize("kk", [2, 5])
+def test_fastconv_full_size_3d_sampled(kk):
+    """64x256x256 U[0,1] conv k^3 N(0,1), sampled outputs and the sum identity."""
+    E = scenes.uniform_array((64, 256, 256), seed=77)
+    k = scenes.normal_array((kk, kk, kk), seed=78)
+    got = _run(E, k)
+    rng = np.random.default_rng(kk)
+    pts = rng.integers(0, got.size, 3000).astype(np.int64)
+    ref, rabs = oracle.fastconv_points(E, k, pts)
+    g = got.reshape(-1)[pts].astype(np.float64)
+    assert np.all(np.abs(g - ref) <= REL * rabs + 1e-30)
+    tot = got.astype(np.float64).sum()
+    expect = E.astype(np.float64).sum() * k.astype(np.float64).sum()
+    scale = np.abs(E).astype(np.float64).sum() * np.abs(k).astype(np.float64).sum()
+    assert abs(tot - expect) <= REL * scale
