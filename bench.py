@@ -345,7 +345,8 @@ def run_ours(args):
         conv_rows, conv_launches = fastconv_sweep(dev, hbm_peak, reps=args.conv_reps)
 
     if rank == 0:
-        algo_bytes = frames_n * H * W + npairs * LEVELS * 72 * 10 * 4
+        # every frame of the video read once + the result records written
+        algo_bytes = frames_n * H * W + npairs * LEVELS * ft.RESULT_DTYPE.itemsize
         achieved = algo_bytes / (tile_ms * 1e-3) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
