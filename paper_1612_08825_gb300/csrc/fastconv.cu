@@ -34,6 +34,7 @@ struct ConvParams {
     int64_t Nr, Nc, Kr, Kc, Mr, Mc;      // plane extents: input, kernel, output
     int64_t tiles_x, tiles_per_plane;
     int vec_in;                          // 1: input rows allow 16-byte loads
+    int vec_out;                         // 1: output rows allow 16-byte stores
 };
 
 // TW = 128 * WX columns, TH = OY * (8 / WX) rows; PADC >= Kc - 1, multiple of 4.
@@ -209,6 +210,159 @@ conv_direct_kernel(const ConvParams p, int64_t total)
     p.out[o] = acc;
 }
 
+// Streaming kernel for small kernels (memory-bound): one warp per 128-column strip
+// and RB output rows of one output plane, no shared memory and no barriers.  Lane l
+// owns output columns ox0 + 4l .. 4l + 3.  Every input row the strip needs is loaded
+// once per warp up front (16-byte loads; all loads in flight together); the KC - 1
+// columns to the left come from lane l - 1 by shuffle (lane 0 loads them).  The KR
+// previous rows of each of the KL input planes stay in registers.
+template <int KL, int KR, int KC, int RB>
+__global__ void __launch_bounds__(kThreads)
+conv_rows_kernel(const ConvParams p, int64_t nstrips, int64_t nrb, int64_t total_warps)
+{
+    constexpr int NROW = RB + KR - 1;            // input rows per warp
+    constexpr int WN = KC + 3;                   // window: KC - 1 halo + 4 own columns
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (wg >= total_warps) return;               // warp-uniform
+    const int64_t plane = wg / (nstrips * nrb);
+    const int64_t rem = wg - plane * nstrips * nrb;
+    const int64_t strip = rem / nrb;
+    const int64_t m0 = (rem - strip * nrb) * RB;
+    const int64_t ox0 = strip * 128;
+    const int64_t c0 = ox0 + 4 * lane;
+
+    // input plane of each leading kernel index (-1: outside the input)
+    int64_t q[KL];
+    {
+        int64_t pm[FT_MAX_NDIM];
+        int64_t r = plane;
+        for (int d = p.nlead - 1; d >= 0; --d) {
+            pm[d] = r % p.out_lead[d];
+            r /= p.out_lead[d];
+        }
+#pragma unroll
+        for (int R = 0; R < KL; ++R) {
+            int64_t qq = 0, rr = R, stride = 1;
+            bool inside = true;
+            for (int d = p.nlead - 1; d >= 0; --d) {
+                const int64_t rd = rr % p.k_lead[d];
+                rr /= p.k_lead[d];
+                const int64_t qd = pm[d] - rd;
+                if (qd < 0 || qd >= p.in_lead[d]) inside = false;
+                qq += qd * stride;
+                stride *= p.in_lead[d];
+            }
+            q[R] = inside ? qq : -1;
+        }
+    }
+    float kr[KL][KR][KC];
+#pragma unroll
+    for (int R = 0; R < KL; ++R)
+#pragma unroll
+        for (int a = 0; a < KR; ++a)
+#pragma unroll
+            for (int b = 0; b < KC; ++b) kr[R][a][b] = __ldg(p.ker + (R * KR + a) * KC + b);
+
+    // phase 1: all loads (own 4 columns; lane 0 also the KC - 1 columns to the left)
+    float own[KL][NROW][4];
+    float left[KL][NROW][KC > 1 ? KC - 1 : 1];
+#pragma unroll
+    for (int R = 0; R < KL; ++R) {
+        const float *src = q[R] >= 0 ? p.in + q[R] * p.Nr * p.Nc : nullptr;
+#pragma unroll
+        for (int t = 0; t < NROW; ++t) {
+            const int64_t gy = m0 - (KR - 1) + t;
+            const bool rok = src != nullptr && gy >= 0 && gy < p.Nr;
+            const float *row = rok ? src + gy * p.Nc : nullptr;
+            if (rok && p.vec_in && c0 + 4 <= p.Nc) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(row + c0));
+                own[R][t][0] = v.x; own[R][t][1] = v.y; own[R][t][2] = v.z; own[R][t][3] = v.w;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) own[R][t][c] = (rok && c0 + c < p.Nc) ? __ldg(row + c0 + c) : 0.f;
+            }
+#pragma unroll
+            for (int b = 0; b < KC - 1; ++b) {
+                const int64_t gx = ox0 - (KC - 1) + b;
+                left[R][t][b] = (lane == 0 && rok && gx >= 0 && gx < p.Nc) ? __ldg(row + gx) : 0.f;
+            }
+        }
+    }
+
+    // phase 2: windows, sums, stores
+    float win[KL][KR][WN];
+    float *dst = p.out + plane * p.Mr * p.Mc;
+#pragma unroll
+    for (int t = 0; t < NROW; ++t) {
+#pragma unroll
+        for (int R = 0; R < KL; ++R) {
+#pragma unroll
+            for (int a = 0; a < KR - 1; ++a)
+#pragma unroll
+                for (int w = 0; w < WN; ++w) win[R][a][w] = win[R][a + 1][w];
+#pragma unroll
+            for (int b = 0; b < KC - 1; ++b) {
+                const float up = __shfl_up_sync(0xffffffffu, own[R][t][4 - (KC - 1) + b], 1);
+                win[R][KR - 1][b] = lane == 0 ? left[R][t][b] : up;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) win[R][KR - 1][KC - 1 + c] = own[R][t][c];
+        }
+        if (t < KR - 1) continue;
+        const int64_t m = m0 + t - (KR - 1);      // output row; window slot a holds row m - (KR-1-a)
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int R = 0; R < KL; ++R)
+#pragma unroll
+            for (int a = 0; a < KR; ++a)          // kernel row a uses input row m - a (slot KR-1-a)
+#pragma unroll
+                for (int b = 0; b < KC; ++b)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        o[c] = fmaf(kr[R][a][b], win[R][KR - 1 - a][c - b + KC - 1], o[c]);
+        if (m < p.Mr) {
+            float *orow = dst + m * p.Mc;
+            if (p.vec_out && c0 + 4 <= p.Mc) {
+                *reinterpret_cast<float4 *>(orow + c0) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (c0 + c < p.Mc) orow[c0 + c] = o[c];
+            }
+        }
+    }
+}
+
+template <int KL, int KR, int KC>
+ft_status launch_rows(const ConvParams &p, int64_t planes, cudaStream_t s)
+{
+    constexpr int RB = 8;
+    const int64_t nstrips = ft::ceil_div(p.Mc, 128);
+    const int64_t nrb = ft::ceil_div(p.Mr, RB);
+    const int64_t warps = planes * nstrips * nrb;
+    const int64_t blocks = ft::ceil_div(warps, kThreads / 32);
+    if (blocks > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
+    conv_rows_kernel<KL, KR, KC, RB><<<(unsigned)blocks, kThreads, 0, s>>>(p, nstrips, nrb, warps);
+    return ft::check_launch();
+}
+
+template <int KL>
+ft_status launch_rows_kl(const ConvParams &p, int64_t planes, cudaStream_t s)
+{
+    switch (p.Kr * 4 + p.Kc) {
+    case 4 * 1 + 1: return launch_rows<KL, 1, 1>(p, planes, s);
+    case 4 * 1 + 2: return launch_rows<KL, 1, 2>(p, planes, s);
+    case 4 * 1 + 3: return launch_rows<KL, 1, 3>(p, planes, s);
+    case 4 * 2 + 1: return launch_rows<KL, 2, 1>(p, planes, s);
+    case 4 * 2 + 2: return launch_rows<KL, 2, 2>(p, planes, s);
+    case 4 * 2 + 3: return launch_rows<KL, 2, 3>(p, planes, s);
+    case 4 * 3 + 1: return launch_rows<KL, 3, 1>(p, planes, s);
+    case 4 * 3 + 2: return launch_rows<KL, 3, 2>(p, planes, s);
+    default: return launch_rows<KL, 3, 3>(p, planes, s);
+    }
+}
+
 template <int PADC, int OY, int WX>
 ft_status launch_tile(const ConvParams &p0, int64_t planes, cudaStream_t s)
 {
@@ -298,6 +452,7 @@ extern "C" ft_status fastconv_nd(const float *input, const int64_t *dims, int nd
     p.Kc = kdims[nd - 1];
     p.Mc = odims[nd - 1];
     p.vec_in = ((reinterpret_cast<uintptr_t>(input) & 15) == 0 && (p.Nc & 3) == 0) ? 1 : 0;
+    p.vec_out = ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && (p.Mc & 3) == 0) ? 1 : 0;
 
     cudaStream_t s = ft::as_stream(stream);
     const bool tiled = p.Kc <= 65 && p.Kr <= 129;
@@ -306,6 +461,11 @@ extern "C" ft_status fastconv_nd(const float *input, const int64_t *dims, int nd
         const unsigned blocks = (unsigned)ft::ceil_div(tot_out, kThreads);
         conv_direct_kernel<<<blocks, kThreads, 0, s>>>(p, tot_out);
         return ft::check_launch();
+    }
+    // small kernels (at most 2 leading taps, plane kernel up to 3 x 3): streaming rows
+    if (p.k_lead_total <= 2 && p.Kr <= 3 && p.Kc <= 3) {
+        if (p.k_lead_total == 1) return launch_rows_kl<1>(p, planes, s);
+        return launch_rows_kl<2>(p, planes, s);
     }
     if (p.Mr == 1) return launch_by_pad<1, 8>(p, planes, s);          // rank 1 (one row)
     if (p.Kr * p.Kc <= 16) return launch_by_pad<4, 1>(p, planes, s);  // small, memory-bound
