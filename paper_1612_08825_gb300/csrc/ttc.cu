@@ -1,7 +1,8 @@
 // Multi-scale time to contact / focus of expansion on sm_103a (Sec. V-A, V-B).
 //
-// Stage 1 (ttc_tile.cuh): the fused pyramid + stencil + G + product + tile-reduction
-// kernel, leaving ten FP32 partial sums per (pair, level, tile).
+// Stage 1 (ttc_pass.cuh): one streaming pass per pyramid level, fusing the 2x2x2
+// stencil, G, the ten products and the tile reduction with the 2x2 block sums of
+// the next level; it leaves ten FP32 partial sums per (level, pair, tile).
 // Stage 2 (ttc_solve_kernel, one warp per pair and level): FP64 merge of the tile
 // partials in a fixed order, scaling to level-l mean-image units, and the FP64
 // solve of the normal equations (Eq. final_TTC).
@@ -12,13 +13,13 @@
 #include <new>
 
 #include "common.cuh"
-#include "ttc_tile.cuh"
+#include "ttc_pass.cuh"
 
 namespace {
 
-using ttc_tile::NSUM;
-using ttc_tile::TR;
-using ttc_tile::TC;
+using ttc_pass::NSUM;
+using ttc_pass::TR;
+using ttc_pass::TC;
 
 // ---------------------------------------------------------------------------
 // stage 2: FP64 merge of the tile partials + solve
@@ -26,7 +27,9 @@ using ttc_tile::TC;
 
 struct SolveParams {
     const float *partials;
-    int ntiles, levels, npairs, mode;
+    int levels, npairs, mode;
+    int ntiles[FT_MAX_LEVELS];        // tiles of level l
+    int64_t poff[FT_MAX_LEVELS];      // level l partials start here: [pair][tile][NSUM]
     double inv_scale[FT_MAX_LEVELS];  // 1 / (16 * 16^l): level-l sums -> mean-image units
     int64_t ncubes[FT_MAX_LEVELS];
     ttc_level_result *out;
@@ -108,11 +111,12 @@ ttc_solve_kernel(const SolveParams p)
     const int item = blockIdx.x;                 // pair * levels + level
     const int pair = item / p.levels, l = item - pair * p.levels;
     const int lane = threadIdx.x;
-    const float *src = p.partials + ((int64_t)pair * p.levels + l) * p.ntiles * NSUM;
+    const int ntiles = p.ntiles[l];
+    const float *src = p.partials + p.poff[l] + (int64_t)pair * ntiles * NSUM;
     double acc[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc[s] = 0.0;
-    for (int t = lane; t < p.ntiles; t += 32)
+    for (int t = lane; t < ntiles; t += 32)
 #pragma unroll
         for (int s = 0; s < NSUM; ++s) acc[s] += (double)src[t * NSUM + s];
 #pragma unroll
@@ -178,21 +182,60 @@ ft_status check_levels(int H, int W, int levels)
     return FT_OK;
 }
 
-void tiling(int H, int W, int &tiles_x, int &tiles_y)
+// Per-level geometry of one request: tiles, partial-sum offsets, and the layout of
+// the level images kept in the context (level l >= 1 of every frame).
+struct Geometry {
+    int levels, npairs, nframes;
+    int H[FT_MAX_LEVELS], W[FT_MAX_LEVELS];
+    int tiles_x[FT_MAX_LEVELS], tiles_y[FT_MAX_LEVELS], ntiles[FT_MAX_LEVELS];
+    int64_t poff[FT_MAX_LEVELS];      // floats
+    int esize[FT_MAX_LEVELS];         // bytes per pixel of the level-l image (l >= 1)
+    int64_t pitch[FT_MAX_LEVELS];     // bytes
+    int64_t fstride[FT_MAX_LEVELS];   // bytes between frames
+    int64_t ioff[FT_MAX_LEVELS];      // bytes, start of level l images
+    int64_t partial_floats, image_bytes;
+};
+
+void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geometry &g)
 {
-    tiles_y = (int)ft::ceil_div(H - 1, TR);
-    tiles_x = (int)ft::ceil_div(W - 1, TC);
+    g.levels = levels;
+    g.npairs = npairs;
+    g.nframes = nframes;
+    int64_t po = 0, io = 0;
+    for (int l = 0; l < levels; ++l) {
+        g.H[l] = H >> l;
+        g.W[l] = W >> l;
+        g.tiles_y[l] = (int)ft::ceil_div(g.H[l] - 1, TR);
+        g.tiles_x[l] = (int)ft::ceil_div(g.W[l] - 1, TC);
+        g.ntiles[l] = g.tiles_y[l] * g.tiles_x[l];
+        g.poff[l] = po;
+        po += (int64_t)npairs * g.ntiles[l] * NSUM;
+        if (l == 0) {
+            g.esize[0] = dtype == FT_U8 ? 1 : 4;
+            g.pitch[0] = g.fstride[0] = g.ioff[0] = 0;
+            continue;
+        }
+        // uint8 frames: exact block sums fit uint16 up to level 4 (255 * 4^4)
+        g.esize[l] = (dtype == FT_U8 && l <= 4) ? 2 : 4;
+        g.pitch[l] = (((int64_t)g.W[l] * g.esize[l]) + 15) / 16 * 16;
+        g.fstride[l] = ((g.pitch[l] * g.H[l]) + 255) / 256 * 256;
+        g.ioff[l] = io;
+        io += g.fstride[l] * nframes;
+    }
+    g.partial_floats = po;
+    g.image_bytes = io;
 }
 
 }  // namespace
 
 struct ttc_ctx {
     int max_H, max_W, max_levels, max_pairs;
-    int max_tiles;
     float *partials;
-    size_t partial_bytes;
-    // geometry of the last ttc_partial_sums call
-    int H, W, levels, npairs, ntiles;
+    unsigned char *images;
+    int64_t partial_cap;      // floats
+    int64_t image_cap;        // bytes
+    size_t bytes;
+    Geometry g;               // of the last ttc_partial_sums call
     bool ready;
 };
 
@@ -203,27 +246,37 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     if (max_pairs < 1 || max_levels < 1) return FT_ERR_INVALID_ARG;
     if (max_H < 2 || max_W < 2) return FT_ERR_SHAPE;
     if (max_levels > FT_MAX_LEVELS) return FT_ERR_UNSUPPORTED;
-    int tx, ty;
-    tiling(max_H, max_W, tx, ty);
-    const size_t bytes = (size_t)max_pairs * max_levels * (size_t)tx * ty * NSUM * sizeof(float);
-    float *buf = nullptr;
-    cudaError_t e = cudaMalloc(&buf, bytes);
+    int lv = 0;
+    while (lv < max_levels && (max_H >> lv) >= 2 && (max_W >> lv) >= 2) ++lv;
+    // the larger of the two layouts: a video of max_pairs + 1 frames or max_pairs
+    // independent pairs (two frames each); float frames need the wider images
+    Geometry g;
+    geometry(max_H, max_W, lv, FT_F32, max_pairs, 2 * max_pairs, g);
+    const int64_t pf = g.partial_floats, ib = g.image_bytes;
+    float *part = nullptr;
+    unsigned char *img = nullptr;
+    cudaError_t e = cudaMalloc(&part, (size_t)pf * sizeof(float));
+    if (e == cudaSuccess && ib > 0) e = cudaMalloc(&img, (size_t)ib);
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
+        cudaFree(part);
         return FT_ERR_CUDA;
     }
     ttc_ctx *c = new (std::nothrow) ttc_ctx();
     if (!c) {
-        cudaFree(buf);
+        cudaFree(part);
+        cudaFree(img);
         return FT_ERR_CUDA;
     }
     c->max_H = max_H;
     c->max_W = max_W;
     c->max_levels = max_levels;
     c->max_pairs = max_pairs;
-    c->max_tiles = tx * ty;
-    c->partials = buf;
-    c->partial_bytes = bytes;
+    c->partials = part;
+    c->images = img;
+    c->partial_cap = pf;
+    c->image_cap = ib;
+    c->bytes = (size_t)pf * sizeof(float) + (size_t)ib;
     c->ready = false;
     *ctx = c;
     return FT_OK;
@@ -233,54 +286,87 @@ extern "C" void ttc_ctx_destroy(ttc_ctx *ctx)
 {
     if (!ctx) return;
     cudaFree(ctx->partials);
+    cudaFree(ctx->images);
     delete ctx;
 }
 
-extern "C" size_t ttc_ctx_workspace_bytes(const ttc_ctx *ctx) { return ctx ? ctx->partial_bytes : 0; }
+extern "C" size_t ttc_ctx_workspace_bytes(const ttc_ctx *ctx) { return ctx ? ctx->bytes : 0; }
 
 namespace {
 
-ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64_t pair_stride,
-                          int npairs, int dtype, int H, int W, int64_t pitch, int levels,
-                          cudaStream_t s)
+template <typename Tin>
+cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs, cudaStream_t s)
+{
+    if (out_esize == 2) return ttc_pass::launch<Tin, unsigned short>(p, npairs, s);
+    return ttc_pass::launch<Tin, float>(p, npairs, s);
+}
+
+// all levels of npairs pairs: pair p is (prev + p * pair_stride, cur + p * pair_stride);
+// independent = 0 for the consecutive pairs of a video (frame t+1 shared)
+ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64_t pair_stride, int npairs,
+                          int independent, int dtype, int H, int W, int64_t pitch, int levels, cudaStream_t s)
 {
     if (!ctx || !prev || !cur) return FT_ERR_INVALID_ARG;
     if (npairs < 1) return FT_ERR_SHAPE;
     ft_status st = check_frames(dtype, H, W, pitch);
     if (st != FT_OK) return st;
     if ((st = check_levels(H, W, levels)) != FT_OK) return st;
-    int tx, ty;
-    tiling(H, W, tx, ty);
-    const int ntiles = tx * ty;
-    if ((size_t)npairs * levels * ntiles > (size_t)ctx->max_pairs * ctx->max_levels * ctx->max_tiles)
+    if (npairs > ctx->max_pairs || levels > ctx->max_levels || H > ctx->max_H || W > ctx->max_W)
         return FT_ERR_WORKSPACE;
-    if ((int64_t)npairs * ntiles > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
+    Geometry g;
+    geometry(H, W, levels, dtype, npairs, independent ? 2 * npairs : npairs + 1, g);
+    if (g.partial_floats > ctx->partial_cap || g.image_bytes > ctx->image_cap) return FT_ERR_WORKSPACE;
+    for (int l = 0; l < levels; ++l)
+        if ((int64_t)npairs * g.ntiles[l] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
 
-    ttc_tile::TileParams p{};
-    p.prev = static_cast<const unsigned char *>(prev);
-    p.cur = static_cast<const unsigned char *>(cur);
-    p.pair_stride = pair_stride;
-    p.pitch = pitch;
-    p.H = H;
-    p.W = W;
-    p.tiles_x = tx;
-    p.ntiles = ntiles;
     const uintptr_t al = dtype == FT_U8 ? 3 : 15;
-    p.vec = ((reinterpret_cast<uintptr_t>(prev) & al) == 0 && (reinterpret_cast<uintptr_t>(cur) & al) == 0 &&
-             (pitch & (int64_t)al) == 0 && (pair_stride & (int64_t)al) == 0) ? 1 : 0;
-    p.partials = ctx->partials;
-    const unsigned blocks = (unsigned)((int64_t)npairs * ntiles);
-    cudaError_t e = dtype == FT_U8 ? ttc_tile::launch<unsigned char>(p, levels, blocks, s)
-                                   : ttc_tile::launch<float>(p, levels, blocks, s);
-    if (e != cudaSuccess) {
-        ft::set_cuda_error(e);
-        return FT_ERR_CUDA;
+    const int vec0 = ((reinterpret_cast<uintptr_t>(prev) & al) == 0 && (reinterpret_cast<uintptr_t>(cur) & al) == 0 &&
+                      (pitch & (int64_t)al) == 0 && (pair_stride & (int64_t)al) == 0) ? 1 : 0;
+    for (int l = 0; l < levels; ++l) {
+        ttc_pass::PassParams p{};
+        if (l == 0) {
+            p.prev = static_cast<const unsigned char *>(prev);
+            p.cur = static_cast<const unsigned char *>(cur);
+            p.pair_stride = pair_stride;
+            p.pitch = pitch;
+            p.all_edge = !vec0;
+        } else {
+            p.prev = ctx->images + g.ioff[l];
+            p.cur = p.prev + g.fstride[l];
+            p.pair_stride = independent ? 2 * g.fstride[l] : g.fstride[l];
+            p.pitch = g.pitch[l];
+            p.all_edge = 0;
+        }
+        p.H = g.H[l];
+        p.W = g.W[l];
+        p.tiles_x = g.tiles_x[l];
+        p.tiles_y = g.tiles_y[l];
+        p.ntiles = g.ntiles[l];
+        // cube centre x = j + 1/2 - cx_l, cx_l = (W - 2^l) / 2^(l+1): the level-0 image
+        // centre (W-1)/2 expressed in level-l pixel indices
+        const double pl = (double)(1 << l);
+        p.xoff = (float)(0.5 - ((double)W - pl) / (2.0 * pl));
+        p.yoff = (float)(0.5 - ((double)H - pl) / (2.0 * pl));
+        p.partials = ctx->partials + g.poff[l];
+        int out_es = 4;
+        if (l + 1 < levels) {
+            p.next = ctx->images + g.ioff[l + 1];
+            p.next_fstride = g.fstride[l + 1];
+            p.next_pitch = g.pitch[l + 1];
+            out_es = g.esize[l + 1];
+        }
+        p.write_prev = independent;
+        const int in_es = g.esize[l];
+        cudaError_t e;
+        if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, npairs, s);
+        else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es, npairs, s);
+        else e = launch_pass<float>(p, out_es, npairs, s);
+        if (e != cudaSuccess) {
+            ft::set_cuda_error(e);
+            return FT_ERR_CUDA;
+        }
     }
-    ctx->H = H;
-    ctx->W = W;
-    ctx->levels = levels;
-    ctx->npairs = npairs;
-    ctx->ntiles = ntiles;
+    ctx->g = g;
     ctx->ready = true;
     return FT_OK;
 }
@@ -290,18 +376,20 @@ ft_status launch_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream
     if (!ctx || !out) return FT_ERR_INVALID_ARG;
     if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
     if (!ctx->ready) return FT_ERR_INVALID_ARG;
+    const Geometry &g = ctx->g;
     SolveParams sp{};
     sp.partials = ctx->partials;
-    sp.ntiles = ctx->ntiles;
-    sp.levels = ctx->levels;
-    sp.npairs = ctx->npairs;
+    sp.levels = g.levels;
+    sp.npairs = g.npairs;
     sp.mode = mode;
-    for (int l = 0; l < ctx->levels; ++l) {
+    for (int l = 0; l < g.levels; ++l) {
+        sp.ntiles[l] = g.ntiles[l];
+        sp.poff[l] = g.poff[l];
         sp.inv_scale[l] = std::ldexp(1.0, -4 - 4 * l);
-        sp.ncubes[l] = (int64_t)((ctx->H >> l) - 1) * (int64_t)((ctx->W >> l) - 1);
+        sp.ncubes[l] = (int64_t)(g.H[l] - 1) * (int64_t)(g.W[l] - 1);
     }
     sp.out = out;
-    ttc_solve_kernel<<<(unsigned)(ctx->npairs * ctx->levels), 32, 0, s>>>(sp);
+    ttc_solve_kernel<<<(unsigned)(g.npairs * g.levels), 32, 0, s>>>(sp);
     return ft::check_launch();
 }
 
@@ -314,7 +402,7 @@ extern "C" ft_status ttc_partial_sums(ttc_ctx *ctx, const void *frames, int64_t 
     if (T < 2) return FT_ERR_SHAPE;
     if (frame_stride_bytes < 0) return FT_ERR_INVALID_ARG;
     const unsigned char *f0 = static_cast<const unsigned char *>(frames);
-    return launch_partials(ctx, f0, f0 + frame_stride_bytes, frame_stride_bytes, T - 1, dtype, H, W,
+    return launch_partials(ctx, f0, f0 + frame_stride_bytes, frame_stride_bytes, T - 1, 0, dtype, H, W,
                            pitch_bytes, levels, ft::as_stream(stream));
 }
 
@@ -329,7 +417,7 @@ extern "C" ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, 
 {
     if (!ctx || !prev || !cur || !out) return FT_ERR_INVALID_ARG;
     if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
-    ft_status st = launch_partials(ctx, prev, cur, 0, 1, dtype, H, W, pitch_bytes, levels,
+    ft_status st = launch_partials(ctx, prev, cur, 0, 1, 0, dtype, H, W, pitch_bytes, levels,
                                    ft::as_stream(stream));
     if (st != FT_OK) return st;
     return launch_solve(ctx, mode, out, ft::as_stream(stream));

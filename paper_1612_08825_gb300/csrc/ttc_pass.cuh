@@ -1,0 +1,429 @@
+// Stage 1 of the multi-scale TTC/FOE solve (Sec. V-A, V-B): one streaming pass per
+// pyramid level.
+//
+// Pass l reads the level-l images of both frames of every pair and produces
+//   - ten FP32 partial sums per tile of TR x TC cubes (0 Ex^2, 1 Ex Ey, 2 Ey^2,
+//     3 G Ex, 4 G Ey, 5 G^2, 6 Ex Et, 7 Ey Et, 8 G Et, 9 Et^2), with Ex, Ey, Et the
+//     2x2x2 first differences of Sec. II scaled by 4 (and by 4^l, because the pyramid
+//     images hold 2x2 block sums rather than means; the merge kernel removes the
+//     scale in FP64) and G = x Ex + y Ey (Sec. V-A);
+//   - from the same loads, the level-(l+1) image (2x2 block sums, floor cropping,
+//     Sec. V-B) of each frame, written once per frame: uint16 for uint8 input up to
+//     level 4 (exact: at most 255 * 4^4), float otherwise (exact up to 2^24).
+// A thread owns 4 columns in the left half of the tile and the same 4 columns in the
+// right half and walks 8 rows (plus one row of overlap); the two halves ride in the
+// two lanes of packed FP32 pairs (add/sub/mul/fma .f32x2).  Integer pixels become
+// floats exactly through the mantissa (2^23 + v assembled by a byte permute, minus
+// 2^23).  The tile sums are reduced in a fixed order through shared memory.
+#pragma once
+
+#include "common.cuh"
+
+namespace ttc_pass {
+
+constexpr int TR = 64;          // cube rows per tile
+constexpr int TC = 256;         // cube columns per tile (two halves of 128)
+constexpr int HALF = TC / 2;
+constexpr int NT = 256;         // threads per CTA
+constexpr int NSUM = 10;
+
+#ifndef FT_TTC_PF
+#define FT_TTC_PF 2             // rows whose loads are issued ahead of the arithmetic
+#endif
+#ifndef FT_TTC_MINB
+#define FT_TTC_MINB 2           // resident CTAs per SM the register allocation must allow
+#endif
+
+struct PassParams {
+    const unsigned char *prev;  // level-l image, first frame of pair 0
+    const unsigned char *cur;   // level-l image, second frame of pair 0
+    int64_t pair_stride;        // bytes from pair p to pair p + 1
+    int64_t pitch;              // bytes between rows of the level-l images
+    int H, W;                   // level-l image size
+    int tiles_x, tiles_y, ntiles;
+    int all_edge;               // 1: the edge kernel covers every tile (rows not vector-loadable)
+    float xoff, yoff;           // cube centre: x = j + xoff, y = i + yoff
+    float *partials;            // this level: [pair][tile][NSUM]
+    unsigned char *next;        // level-(l+1) image of frame 0, or null
+    int64_t next_fstride;       // bytes between frames of `next`
+    int64_t next_pitch;         // bytes between rows of `next`
+    int write_prev;             // 0: video (frame t+1 of pair t is shared); 1: independent pairs
+};
+
+// ---------------------------------------------------------------------------
+// packed FP32 pairs
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long r;
+    const unsigned long long x = *reinterpret_cast<const unsigned long long *>(&a);
+    const unsigned long long y = *reinterpret_cast<const unsigned long long *>(&b);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    return *reinterpret_cast<const float2 *>(&r);
+}
+
+// the ten products of two cubes (one per lane of the pair)
+__device__ __forceinline__ void accum2(float2 acc[NSUM], float2 ex, float2 ey, float2 et, float2 x, float2 y)
+{
+    const float2 g = fma2(x, ex, mul2(y, ey));
+    acc[0] = fma2(ex, ex, acc[0]);
+    acc[1] = fma2(ex, ey, acc[1]);
+    acc[2] = fma2(ey, ey, acc[2]);
+    acc[3] = fma2(g, ex, acc[3]);
+    acc[4] = fma2(g, ey, acc[4]);
+    acc[5] = fma2(g, g, acc[5]);
+    acc[6] = fma2(ex, et, acc[6]);
+    acc[7] = fma2(ey, et, acc[7]);
+    acc[8] = fma2(g, et, acc[8]);
+    acc[9] = fma2(et, et, acc[9]);
+}
+
+// Fixed-order CTA reduction of ten per-thread values to dst[0..9] (global):
+// shared-memory transpose, 16-way strided sums, 16-lane shuffle tree.
+__device__ __forceinline__ void block_reduce(const float acc[NSUM], float *red, float *dst)
+{
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int s = 0; s < NSUM; ++s) red[s * NT + tid] = acc[s];
+    __syncthreads();
+    if (tid < NSUM * 16) {
+        const int s = tid >> 4, l = tid & 15;
+        float v = 0.f;
+#pragma unroll
+        for (int k = 0; k < NT / 16; ++k) v += red[s * NT + l + 16 * k];
+#pragma unroll
+        for (int o = 8; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (l == 0) dst[s] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pixel types
+// ---------------------------------------------------------------------------
+
+// exact float of an unsigned integer v < 2^23 held in bytes of w: the selector puts
+// v in the low mantissa bytes under the exponent of 2^23; the bias is removed later
+__device__ __forceinline__ float biased(uint32_t w, uint32_t sel)
+{
+    return __int_as_float(__byte_perm(w, 0x4B000000u, sel));
+}
+__device__ __forceinline__ float2 unbias2(float2 v) { return add2(v, make_float2(-8388608.f, -8388608.f)); }
+
+template <typename T> struct Pix;
+
+template <> struct Pix<unsigned char> {
+    using Vec = uint32_t;                       // 4 pixels
+    static constexpr bool INT = true;
+    __device__ static Vec ld4(const unsigned char *p) { return __ldg(reinterpret_cast<const unsigned int *>(p)); }
+    __device__ static Vec zero() { return 0u; }
+    __device__ static float elem_biased(const Vec &v, int k) { return biased(v, 0x7540u | (uint32_t)k); }
+    __device__ static float ld1(const unsigned char *p) { return (float)__ldg(p); }
+};
+
+template <> struct Pix<unsigned short> {
+    using Vec = uint2;                          // 4 pixels
+    static constexpr bool INT = true;
+    __device__ static Vec ld4(const unsigned short *p) { return __ldg(reinterpret_cast<const uint2 *>(p)); }
+    __device__ static Vec zero() { return make_uint2(0u, 0u); }
+    __device__ static float elem_biased(const Vec &v, int k)
+    {
+        return biased(k < 2 ? v.x : v.y, (k & 1) ? 0x7532u : 0x7510u);
+    }
+    __device__ static float ld1(const unsigned short *p) { return (float)__ldg(p); }
+};
+
+template <> struct Pix<float> {
+    using Vec = float4;
+    static constexpr bool INT = false;
+    __device__ static Vec ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    __device__ static Vec zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static float elem_biased(const Vec &v, int k)
+    {
+        return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+    }
+    __device__ static float ld1(const float *p) { return __ldg(p); }
+};
+
+// raw loads of one row of both frames: 4 columns in each half + the column right of
+// the right half (used by lane 31 only); zero outside the image
+template <typename T> struct RawRow {
+    typename Pix<T>::Vec al, ar, bl, br;
+    float a4, b4;
+};
+
+__device__ __forceinline__ uint32_t load4_checked(const unsigned char *row, int col, int W, bool rowok)
+{
+    uint32_t w = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool ok = rowok && col + k < W;
+        const uint32_t v = __ldg(row + (ok ? col + k : 0));
+        w |= (ok ? v : 0u) << (8 * k);
+    }
+    return w;
+}
+__device__ __forceinline__ uint2 load4_checked(const unsigned short *row, int col, int W, bool rowok)
+{
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool ok = rowok && col + k < W;
+        const uint32_t x = __ldg(row + (ok ? col + k : 0));
+        v[k] = ok ? x : 0u;
+    }
+    return make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
+}
+__device__ __forceinline__ float4 load4_checked(const float *row, int col, int W, bool rowok)
+{
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool ok = rowok && col + k < W;
+        const float x = __ldg(row + (ok ? col + k : 0));
+        v[k] = ok ? x : 0.f;
+    }
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+template <typename T, bool ROWCHK, bool COLCHK, bool VEC>
+__device__ __forceinline__ void load_raw(const PassParams &p, const T *fa, const T *fb, int gy, int gcl, RawRow<T> &r)
+{
+    const bool rowok = !ROWCHK || gy < p.H;
+    const int gyc = ROWCHK ? min(gy, p.H - 1) : gy;
+    const int64_t pe = p.pitch / (int64_t)sizeof(T);
+    const T *ra = fa + (int64_t)gyc * pe;
+    const T *rb = fb + (int64_t)gyc * pe;
+    const int gcr = gcl + HALF;
+    if (!COLCHK && VEC) {
+        const typename Pix<T>::Vec z = Pix<T>::zero();
+        const typename Pix<T>::Vec al = Pix<T>::ld4(ra + gcl), ar = Pix<T>::ld4(ra + gcr);
+        const typename Pix<T>::Vec bl = Pix<T>::ld4(rb + gcl), br = Pix<T>::ld4(rb + gcr);
+        r.al = rowok ? al : z;
+        r.ar = rowok ? ar : z;
+        r.bl = rowok ? bl : z;
+        r.br = rowok ? br : z;
+    } else {
+        r.al = load4_checked(ra, gcl, p.W, rowok);
+        r.ar = load4_checked(ra, gcr, p.W, rowok);
+        r.bl = load4_checked(rb, gcl, p.W, rowok);
+        r.br = load4_checked(rb, gcr, p.W, rowok);
+    }
+    const int c4 = gcr + 4;
+    const bool ok4 = rowok && (!COLCHK || c4 < p.W);
+    const int c4c = ok4 ? c4 : 0;
+    const float va = Pix<T>::ld1(ra + c4c), vb = Pix<T>::ld1(rb + c4c);
+    r.a4 = ok4 ? va : 0.f;
+    r.b4 = ok4 ? vb : 0.f;
+}
+
+// (left, right) float pairs of the 5 columns; the neighbour column of the left half
+// comes from lane+1 (lane 31: the first right-half column, held by lane 0), that of
+// the right half from lane+1 (lane 31: its own load)
+template <typename T>
+__device__ __forceinline__ void unpack5(const RawRow<T> &r, int lane, float2 A[5], float2 B[5])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        A[k] = make_float2(Pix<T>::elem_biased(r.al, k), Pix<T>::elem_biased(r.ar, k));
+        B[k] = make_float2(Pix<T>::elem_biased(r.bl, k), Pix<T>::elem_biased(r.br, k));
+        if (Pix<T>::INT) {
+            A[k] = unbias2(A[k]);
+            B[k] = unbias2(B[k]);
+        }
+    }
+    const int src = (lane + 1) & 31;
+    const float a4l = __shfl_sync(0xffffffffu, lane == 0 ? A[0].y : A[0].x, src);
+    const float b4l = __shfl_sync(0xffffffffu, lane == 0 ? B[0].y : B[0].x, src);
+    const float a4r = __shfl_sync(0xffffffffu, A[0].y, src);
+    const float b4r = __shfl_sync(0xffffffffu, B[0].y, src);
+    A[4] = make_float2(a4l, lane == 31 ? r.a4 : a4r);
+    B[4] = make_float2(b4l, lane == 31 ? r.b4 : b4r);
+}
+
+__device__ __forceinline__ void mask3(float2 &ex, float2 &ey, float2 &et, bool okl, bool okr)
+{
+    ex = make_float2(okl ? ex.x : 0.f, okr ? ex.y : 0.f);
+    ey = make_float2(okl ? ey.x : 0.f, okr ? ey.y : 0.f);
+    et = make_float2(okl ? et.x : 0.f, okr ? et.y : 0.f);
+}
+
+// One row step: previous row (ps = prev + cur, pd = cur - prev, per column) and the
+// current row A (prev frame), B (cur frame) give the 4 cube pairs of the previous
+// row.  Columns are streamed left to right (two-column window of intermediates).
+template <bool EDGE>
+__device__ __forceinline__ void strip_row(const float2 A[5], const float2 B[5], float2 ps[5], float2 pd[5],
+                                          bool first, float2 x0, float yv, bool rowok, int jl, int jr,
+                                          int Wlim, float2 acc[NSUM])
+{
+    const float2 y = make_float2(yv, yv);
+    float2 cs_p, vd_p, td_p;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float2 s = add2(A[k], B[k]);
+        const float2 d = sub2(B[k], A[k]);
+        if (!first) {
+            const float2 cs = add2(s, ps[k]);     // column sum over 2 rows x 2 frames
+            const float2 vd = sub2(s, ps[k]);     // row difference, both frames
+            const float2 td = add2(d, pd[k]);     // time difference, both rows
+            if (k > 0) {
+                float2 ex = sub2(cs, cs_p);
+                float2 ey = add2(vd_p, vd);
+                float2 et = add2(td_p, td);
+                if (EDGE) mask3(ex, ey, et, rowok && (jl + k - 1 < Wlim), rowok && (jr + k - 1 < Wlim));
+                const float kk = (float)(k - 1);
+                accum2(acc, ex, ey, et, add2(x0, make_float2(kk, kk)), y);
+            }
+            cs_p = cs;
+            vd_p = vd;
+            td_p = td;
+        }
+        ps[k] = s;
+        pd[k] = d;
+    }
+}
+
+// level-(l+1) pixels (row r1, columns c and c+1) of one frame from the thread's 2x2
+// block sums, written if they exist (r1 < H/2, column < W/2)
+template <typename Tout, bool EDGE>
+__device__ __forceinline__ void store_next(unsigned char *img, int64_t pitch, int r1, int c, float v0, float v1,
+                                           int Hn, int Wn)
+{
+    if (EDGE && r1 >= Hn) return;
+    Tout *row = reinterpret_cast<Tout *>(img + (int64_t)r1 * pitch);
+    if (!EDGE || c + 1 < Wn) {
+        if (sizeof(Tout) == 2) {
+            // exact integers < 2^16: their bits are the low mantissa bits of 2^23 + v
+            const uint32_t lo = __float_as_uint(v0 + 8388608.f) & 0xffffu;
+            const uint32_t hi = __float_as_uint(v1 + 8388608.f) << 16;
+            *reinterpret_cast<uint32_t *>(row + c) = lo | hi;
+        } else {
+            *reinterpret_cast<float2 *>(row + c) = make_float2(v0, v1);
+        }
+    } else if (c < Wn) {
+        row[c] = sizeof(Tout) == 2 ? (Tout)(__float_as_uint(v0 + 8388608.f) & 0xffffu) : (Tout)v0;
+    }
+}
+
+template <typename Tin, typename Tout, bool EDGE, bool VEC, bool WRITE>
+__device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, const Tin *fb, int pair, int R0,
+                                          int C0, float2 acc[NSUM])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gcl = C0 + 4 * lane;
+    const int gr0 = R0 + 8 * warp;
+    const float2 x0 = make_float2((float)gcl + p.xoff, (float)(gcl + HALF) + p.xoff);
+    const int Hn = p.H >> 1, Wn = p.W >> 1;
+    // consecutive pairs of a video share frames (frame t+1 of pair t is frame t+1 of
+    // the next pair): the first frame is written by pair 0 only; independent pairs
+    // own two frames each
+    const bool wprev = WRITE && (p.write_prev || pair == 0);
+    const int64_t fprev = p.write_prev ? 2 * (int64_t)pair : (int64_t)pair;
+    unsigned char *nprev = WRITE ? p.next + fprev * p.next_fstride : nullptr;
+    unsigned char *ncur = WRITE ? nprev + p.next_fstride : nullptr;
+
+    constexpr int PF = EDGE ? 1 : FT_TTC_PF;
+    RawRow<Tin> raw[9];
+#pragma unroll
+    for (int r = 0; r < PF; ++r) load_raw<Tin, EDGE, EDGE, VEC>(p, fa, fb, gr0 + r, gcl, raw[r]);
+
+    float2 ps[5], pd[5], ha[2], hb[2];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        if (r + PF < 9) load_raw<Tin, EDGE, EDGE, VEC>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
+        float2 A[5], B[5];
+        unpack5(raw[r], lane, A, B);
+        const int i = gr0 + r - 1;
+        strip_row<EDGE>(A, B, ps, pd, r == 0, x0, (float)i + p.yoff, i < p.H - 1, gcl, gcl + HALF, p.W - 1, acc);
+        if (WRITE && r < 8) {
+            if ((r & 1) == 0) {
+                ha[0] = add2(A[0], A[1]); ha[1] = add2(A[2], A[3]);
+                hb[0] = add2(B[0], B[1]); hb[1] = add2(B[2], B[3]);
+            } else {
+                const float2 va0 = add2(ha[0], add2(A[0], A[1]));
+                const float2 va1 = add2(ha[1], add2(A[2], A[3]));
+                const float2 vb0 = add2(hb[0], add2(B[0], B[1]));
+                const float2 vb1 = add2(hb[1], add2(B[2], B[3]));
+                const int r1 = (gr0 >> 1) + (r >> 1);
+                const int cl = gcl >> 1, cr = (gcl + HALF) >> 1;
+                store_next<Tout, EDGE>(ncur, p.next_pitch, r1, cl, vb0.x, vb1.x, Hn, Wn);
+                store_next<Tout, EDGE>(ncur, p.next_pitch, r1, cr, vb0.y, vb1.y, Hn, Wn);
+                if (wprev) {
+                    store_next<Tout, EDGE>(nprev, p.next_pitch, r1, cl, va0.x, va1.x, Hn, Wn);
+                    store_next<Tout, EDGE>(nprev, p.next_pitch, r1, cr, va0.y, va1.y, Hn, Wn);
+                }
+            }
+        }
+    }
+}
+
+// EDGE = false: the interior tiles (every row and column read lies inside the image;
+// 16/8/4-byte vector loads, no masks), grid npairs x (tiles_y - 1) x (tiles_x - 1).
+// EDGE = true: the last tile row and column (grid npairs x (tiles_x + tiles_y - 1)),
+// or every tile when all_edge is set; element loads with bounds checks.
+template <typename Tin, typename Tout, bool WRITE, bool EDGE>
+__global__ void __launch_bounds__(NT, FT_TTC_MINB)
+ttc_pass_kernel(const PassParams p)
+{
+    __shared__ float red[NSUM * NT];
+    const int64_t bid = blockIdx.x;
+    int pair, ty, tx;
+    if (!EDGE) {
+        const int ix = p.tiles_x - 1, ni = (p.tiles_y - 1) * ix;
+        pair = (int)(bid / ni);
+        const int t = (int)(bid - (int64_t)pair * ni);
+        ty = t / ix;
+        tx = t - ty * ix;
+    } else if (p.all_edge) {
+        pair = (int)(bid / p.ntiles);
+        const int t = (int)(bid - (int64_t)pair * p.ntiles);
+        ty = t / p.tiles_x;
+        tx = t - ty * p.tiles_x;
+    } else {
+        const int ne = p.tiles_x + p.tiles_y - 1;
+        pair = (int)(bid / ne);
+        const int e = (int)(bid - (int64_t)pair * ne);
+        if (e < p.tiles_x) {
+            ty = p.tiles_y - 1;
+            tx = e;
+        } else {
+            ty = e - p.tiles_x;
+            tx = p.tiles_x - 1;
+        }
+    }
+    const int tile = ty * p.tiles_x + tx;
+    const int R0 = ty * TR, C0 = tx * TC;
+    const Tin *fa = reinterpret_cast<const Tin *>(p.prev + (int64_t)pair * p.pair_stride);
+    const Tin *fb = reinterpret_cast<const Tin *>(p.cur + (int64_t)pair * p.pair_stride);
+
+    float2 acc2[NSUM];
+#pragma unroll
+    for (int s = 0; s < NSUM; ++s) acc2[s] = make_float2(0.f, 0.f);
+    pass_body<Tin, Tout, EDGE, !EDGE, WRITE>(p, fa, fb, pair, R0, C0, acc2);
+    float acc[NSUM];
+#pragma unroll
+    for (int s = 0; s < NSUM; ++s) acc[s] = acc2[s].x + acc2[s].y;
+    block_reduce(acc, red, p.partials + ((int64_t)pair * p.ntiles + tile) * NSUM);
+}
+
+template <typename Tin, typename Tout, bool WRITE>
+cudaError_t launch_w(const PassParams &p, int npairs, cudaStream_t s)
+{
+    const int64_t interior = p.all_edge ? 0 : (int64_t)(p.tiles_y - 1) * (p.tiles_x - 1);
+    const int64_t edge = p.all_edge ? p.ntiles : (int64_t)(p.tiles_x + p.tiles_y - 1);
+    if (interior > 0)
+        ttc_pass_kernel<Tin, Tout, WRITE, false><<<(unsigned)(interior * npairs), NT, 0, s>>>(p);
+    ttc_pass_kernel<Tin, Tout, WRITE, true><<<(unsigned)(edge * npairs), NT, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch(const PassParams &p, int npairs, cudaStream_t s)
+{
+    return p.next ? launch_w<Tin, Tout, true>(p, npairs, s) : launch_w<Tin, Tout, false>(p, npairs, s);
+}
+
+}  // namespace ttc_pass
