@@ -217,8 +217,10 @@ void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geom
         }
         // uint8 frames: exact block sums fit uint16 up to level 4 (255 * 4^4)
         g.esize[l] = (dtype == FT_U8 && l <= 4) ? 2 : 4;
-        g.pitch[l] = (((int64_t)g.W[l] * g.esize[l]) + 15) / 16 * 16;
-        g.fstride[l] = ((g.pitch[l] * g.H[l]) + 255) / 256 * 256;
+        // padded so that every tile of the pass reads inside the allocation: columns up
+        // to tiles_x * TC (+ one), rows up to tiles_y * TR (+ one)
+        g.pitch[l] = (((int64_t)(g.tiles_x[l] * TC + 8) * g.esize[l]) + 15) / 16 * 16;
+        g.fstride[l] = ((g.pitch[l] * (g.tiles_y[l] * TR + 1)) + 255) / 256 * 256;
         g.ioff[l] = io;
         io += g.fstride[l] * nframes;
     }
@@ -295,10 +297,11 @@ extern "C" size_t ttc_ctx_workspace_bytes(const ttc_ctx *ctx) { return ctx ? ctx
 namespace {
 
 template <typename Tin>
-cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs, cudaStream_t s)
+cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int level, int vec, int npairs,
+                        cudaStream_t s)
 {
-    if (out_esize == 2) return ttc_pass::launch<Tin, unsigned short>(p, npairs, s);
-    return ttc_pass::launch<Tin, float>(p, npairs, s);
+    if (out_esize == 2) return ttc_pass::launch<Tin, unsigned short>(p, level, vec, npairs, s);
+    return ttc_pass::launch<Tin, float>(p, level, vec, npairs, s);
 }
 
 // all levels of npairs pairs: pair p is (prev + p * pair_stride, cur + p * pair_stride);
@@ -329,13 +332,11 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
             p.cur = static_cast<const unsigned char *>(cur);
             p.pair_stride = pair_stride;
             p.pitch = pitch;
-            p.all_edge = !vec0;
         } else {
             p.prev = ctx->images + g.ioff[l];
             p.cur = p.prev + g.fstride[l];
             p.pair_stride = independent ? 2 * g.fstride[l] : g.fstride[l];
             p.pitch = g.pitch[l];
-            p.all_edge = 0;
         }
         p.H = g.H[l];
         p.W = g.W[l];
@@ -358,9 +359,10 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
         p.write_prev = independent;
         const int in_es = g.esize[l];
         cudaError_t e;
-        if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, npairs, s);
-        else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es, npairs, s);
-        else e = launch_pass<float>(p, out_es, npairs, s);
+        const int vec = l == 0 ? vec0 : 1;
+        if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, l, vec, npairs, s);
+        else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es, l, vec, npairs, s);
+        else e = launch_pass<float>(p, out_es, l, vec, npairs, s);
         if (e != cudaSuccess) {
             ft::set_cuda_error(e);
             return FT_ERR_CUDA;

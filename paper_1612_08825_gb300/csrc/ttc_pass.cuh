@@ -34,6 +34,9 @@ constexpr int NSUM = 10;
 #define FT_TTC_MINB 2           // resident CTAs per SM the register allocation must allow
 #endif
 
+// tile sets of one launch
+enum TileSet { SET_INTERIOR = 0, SET_BOTTOM = 1, SET_RIGHT = 2, SET_EDGES = 3, SET_ALL = 4 };
+
 struct PassParams {
     const unsigned char *prev;  // level-l image, first frame of pair 0
     const unsigned char *cur;   // level-l image, second frame of pair 0
@@ -41,7 +44,7 @@ struct PassParams {
     int64_t pitch;              // bytes between rows of the level-l images
     int H, W;                   // level-l image size
     int tiles_x, tiles_y, ntiles;
-    int all_edge;               // 1: the edge kernel covers every tile (rows not vector-loadable)
+    int set;                    // which tiles this launch covers (TileSet)
     float xoff, yoff;           // cube centre: x = j + xoff, y = i + yoff
     float *partials;            // this level: [pair][tile][NSUM]
     unsigned char *next;        // level-(l+1) image of frame 0, or null
@@ -308,7 +311,7 @@ __device__ __forceinline__ void store_next(unsigned char *img, int64_t pitch, in
     }
 }
 
-template <typename Tin, typename Tout, bool EDGE, bool VEC, bool WRITE>
+template <typename Tin, typename Tout, bool ROWCHK, bool COLCHK, bool MASK, bool WRITE>
 __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, const Tin *fb, int pair, int R0,
                                           int C0, float2 acc[NSUM])
 {
@@ -325,19 +328,19 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
     unsigned char *nprev = WRITE ? p.next + fprev * p.next_fstride : nullptr;
     unsigned char *ncur = WRITE ? nprev + p.next_fstride : nullptr;
 
-    constexpr int PF = EDGE ? 1 : FT_TTC_PF;
+    constexpr int PF = COLCHK ? 1 : FT_TTC_PF;
     RawRow<Tin> raw[9];
 #pragma unroll
-    for (int r = 0; r < PF; ++r) load_raw<Tin, EDGE, EDGE, VEC>(p, fa, fb, gr0 + r, gcl, raw[r]);
+    for (int r = 0; r < PF; ++r) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r, gcl, raw[r]);
 
     float2 ps[5], pd[5], ha[2], hb[2];
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
-        if (r + PF < 9) load_raw<Tin, EDGE, EDGE, VEC>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
+        if (r + PF < 9) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
         float2 A[5], B[5];
         unpack5(raw[r], lane, A, B);
         const int i = gr0 + r - 1;
-        strip_row<EDGE>(A, B, ps, pd, r == 0, x0, (float)i + p.yoff, i < p.H - 1, gcl, gcl + HALF, p.W - 1, acc);
+        strip_row<MASK>(A, B, ps, pd, r == 0, x0, (float)i + p.yoff, i < p.H - 1, gcl, gcl + HALF, p.W - 1, acc);
         if (WRITE && r < 8) {
             if ((r & 1) == 0) {
                 ha[0] = add2(A[0], A[1]); ha[1] = add2(A[2], A[3]);
@@ -349,51 +352,64 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
                 const float2 vb1 = add2(hb[1], add2(B[2], B[3]));
                 const int r1 = (gr0 >> 1) + (r >> 1);
                 const int cl = gcl >> 1, cr = (gcl + HALF) >> 1;
-                store_next<Tout, EDGE>(ncur, p.next_pitch, r1, cl, vb0.x, vb1.x, Hn, Wn);
-                store_next<Tout, EDGE>(ncur, p.next_pitch, r1, cr, vb0.y, vb1.y, Hn, Wn);
+                store_next<Tout, MASK>(ncur, p.next_pitch, r1, cl, vb0.x, vb1.x, Hn, Wn);
+                store_next<Tout, MASK>(ncur, p.next_pitch, r1, cr, vb0.y, vb1.y, Hn, Wn);
                 if (wprev) {
-                    store_next<Tout, EDGE>(nprev, p.next_pitch, r1, cl, va0.x, va1.x, Hn, Wn);
-                    store_next<Tout, EDGE>(nprev, p.next_pitch, r1, cr, va0.y, va1.y, Hn, Wn);
+                    store_next<Tout, MASK>(nprev, p.next_pitch, r1, cl, va0.x, va1.x, Hn, Wn);
+                    store_next<Tout, MASK>(nprev, p.next_pitch, r1, cr, va0.y, va1.y, Hn, Wn);
                 }
             }
         }
     }
 }
 
-// EDGE = false: the interior tiles (every row and column read lies inside the image;
-// 16/8/4-byte vector loads, no masks), grid npairs x (tiles_y - 1) x (tiles_x - 1).
-// EDGE = true: the last tile row and column (grid npairs x (tiles_x + tiles_y - 1)),
-// or every tile when all_edge is set; element loads with bounds checks.
-template <typename Tin, typename Tout, bool WRITE, bool EDGE>
+// Tile sets and checks.  Interior tiles read only inside the image: vector loads, no
+// masks.  The bottom tile row of a level-0 frame clamps rows past the image (columns
+// stay inside).  The right tile column of a level-0 frame checks every element.  The
+// images of levels >= 1 are padded by the context so that every tile reads inside its
+// allocation: their edge tiles use vector loads and only mask the cubes.
+__device__ __forceinline__ void decode_tile(const PassParams &p, int64_t bid, int &pair, int &ty, int &tx)
+{
+    int n;
+    switch (p.set) {
+    case SET_INTERIOR: n = (p.tiles_y - 1) * (p.tiles_x - 1); break;
+    case SET_BOTTOM: n = p.tiles_x - 1; break;
+    case SET_RIGHT: n = p.tiles_y; break;
+    case SET_EDGES: n = p.tiles_x + p.tiles_y - 1; break;
+    default: n = p.ntiles; break;
+    }
+    pair = (int)(bid / n);
+    const int t = (int)(bid - (int64_t)pair * n);
+    switch (p.set) {
+    case SET_INTERIOR: ty = t / (p.tiles_x - 1); tx = t - ty * (p.tiles_x - 1); break;
+    case SET_BOTTOM: ty = p.tiles_y - 1; tx = t; break;
+    case SET_RIGHT: ty = t; tx = p.tiles_x - 1; break;
+    case SET_EDGES:
+        if (t < p.tiles_x) { ty = p.tiles_y - 1; tx = t; }
+        else { ty = t - p.tiles_x; tx = p.tiles_x - 1; }
+        break;
+    default: ty = t / p.tiles_x; tx = t - ty * p.tiles_x; break;
+    }
+}
+
+inline int64_t set_size(const PassParams &p)
+{
+    switch (p.set) {
+    case SET_INTERIOR: return (int64_t)(p.tiles_y - 1) * (p.tiles_x - 1);
+    case SET_BOTTOM: return p.tiles_x - 1;
+    case SET_RIGHT: return p.tiles_y;
+    case SET_EDGES: return p.tiles_x + p.tiles_y - 1;
+    default: return p.ntiles;
+    }
+}
+
+template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK>
 __global__ void __launch_bounds__(NT, FT_TTC_MINB)
 ttc_pass_kernel(const PassParams p)
 {
     __shared__ float red[NSUM * NT];
-    const int64_t bid = blockIdx.x;
     int pair, ty, tx;
-    if (!EDGE) {
-        const int ix = p.tiles_x - 1, ni = (p.tiles_y - 1) * ix;
-        pair = (int)(bid / ni);
-        const int t = (int)(bid - (int64_t)pair * ni);
-        ty = t / ix;
-        tx = t - ty * ix;
-    } else if (p.all_edge) {
-        pair = (int)(bid / p.ntiles);
-        const int t = (int)(bid - (int64_t)pair * p.ntiles);
-        ty = t / p.tiles_x;
-        tx = t - ty * p.tiles_x;
-    } else {
-        const int ne = p.tiles_x + p.tiles_y - 1;
-        pair = (int)(bid / ne);
-        const int e = (int)(bid - (int64_t)pair * ne);
-        if (e < p.tiles_x) {
-            ty = p.tiles_y - 1;
-            tx = e;
-        } else {
-            ty = e - p.tiles_x;
-            tx = p.tiles_x - 1;
-        }
-    }
+    decode_tile(p, blockIdx.x, pair, ty, tx);
     const int tile = ty * p.tiles_x + tx;
     const int R0 = ty * TR, C0 = tx * TC;
     const Tin *fa = reinterpret_cast<const Tin *>(p.prev + (int64_t)pair * p.pair_stride);
@@ -402,28 +418,44 @@ ttc_pass_kernel(const PassParams p)
     float2 acc2[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc2[s] = make_float2(0.f, 0.f);
-    pass_body<Tin, Tout, EDGE, !EDGE, WRITE>(p, fa, fb, pair, R0, C0, acc2);
+    pass_body<Tin, Tout, ROWCHK, COLCHK, MASK, WRITE>(p, fa, fb, pair, R0, C0, acc2);
     float acc[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc[s] = acc2[s].x + acc2[s].y;
     block_reduce(acc, red, p.partials + ((int64_t)pair * p.ntiles + tile) * NSUM);
 }
 
-template <typename Tin, typename Tout, bool WRITE>
-cudaError_t launch_w(const PassParams &p, int npairs, cudaStream_t s)
+template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK>
+void launch_set(PassParams p, int set, int npairs, cudaStream_t s)
 {
-    const int64_t interior = p.all_edge ? 0 : (int64_t)(p.tiles_y - 1) * (p.tiles_x - 1);
-    const int64_t edge = p.all_edge ? p.ntiles : (int64_t)(p.tiles_x + p.tiles_y - 1);
-    if (interior > 0)
-        ttc_pass_kernel<Tin, Tout, WRITE, false><<<(unsigned)(interior * npairs), NT, 0, s>>>(p);
-    ttc_pass_kernel<Tin, Tout, WRITE, true><<<(unsigned)(edge * npairs), NT, 0, s>>>(p);
+    p.set = set;
+    const int64_t n = set_size(p) * npairs;
+    if (n > 0) ttc_pass_kernel<Tin, Tout, WRITE, ROWCHK, COLCHK, MASK><<<(unsigned)n, NT, 0, s>>>(p);
+}
+
+// level: 0 reads the caller's frames (vec: rows allow vector loads), >= 1 the padded
+// context images
+template <typename Tin, typename Tout, bool WRITE>
+cudaError_t launch_w(const PassParams &p, int level, int vec, int npairs, cudaStream_t s)
+{
+    if (level > 0) {
+        launch_set<Tin, Tout, WRITE, false, false, false>(p, SET_INTERIOR, npairs, s);
+        launch_set<Tin, Tout, WRITE, false, false, true>(p, SET_EDGES, npairs, s);
+    } else if (vec) {
+        launch_set<Tin, Tout, WRITE, false, false, false>(p, SET_INTERIOR, npairs, s);
+        launch_set<Tin, Tout, WRITE, true, false, true>(p, SET_BOTTOM, npairs, s);
+        launch_set<Tin, Tout, WRITE, true, true, true>(p, SET_RIGHT, npairs, s);
+    } else {
+        launch_set<Tin, Tout, WRITE, true, true, true>(p, SET_ALL, npairs, s);
+    }
     return cudaGetLastError();
 }
 
 template <typename Tin, typename Tout>
-cudaError_t launch(const PassParams &p, int npairs, cudaStream_t s)
+cudaError_t launch(const PassParams &p, int level, int vec, int npairs, cudaStream_t s)
 {
-    return p.next ? launch_w<Tin, Tout, true>(p, npairs, s) : launch_w<Tin, Tout, false>(p, npairs, s);
+    return p.next ? launch_w<Tin, Tout, true>(p, level, vec, npairs, s)
+                  : launch_w<Tin, Tout, false>(p, level, vec, npairs, s);
 }
 
 }  // namespace ttc_pass
