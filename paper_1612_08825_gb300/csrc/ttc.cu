@@ -217,10 +217,11 @@ void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geom
         }
         // uint8 frames: exact block sums fit uint16 up to level 4 (255 * 4^4)
         g.esize[l] = (dtype == FT_U8 && l <= 4) ? 2 : 4;
-        // padded so that every tile of the pass reads inside the allocation: columns up
-        // to tiles_x * TC (+ one), rows up to tiles_y * TR (+ one)
+        // padded so that every tile of the pass reads inside the allocation: shifted
+        // edge tiles read up to row H and column W + 2 (tiles_y * TR >= H - 1,
+        // tiles_x * TC >= W - 1)
         g.pitch[l] = (((int64_t)(g.tiles_x[l] * TC + 8) * g.esize[l]) + 15) / 16 * 16;
-        g.fstride[l] = ((g.pitch[l] * (g.tiles_y[l] * TR + 1)) + 255) / 256 * 256;
+        g.fstride[l] = ((g.pitch[l] * (g.tiles_y[l] * TR + 2)) + 255) / 256 * 256;
         g.ioff[l] = io;
         io += g.fstride[l] * nframes;
     }
@@ -297,11 +298,10 @@ extern "C" size_t ttc_ctx_workspace_bytes(const ttc_ctx *ctx) { return ctx ? ctx
 namespace {
 
 template <typename Tin>
-cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int level, int vec, int npairs,
-                        cudaStream_t s)
+cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs, cudaStream_t s)
 {
-    if (out_esize == 2) return ttc_pass::launch<Tin, unsigned short>(p, level, vec, npairs, s);
-    return ttc_pass::launch<Tin, float>(p, level, vec, npairs, s);
+    if (out_esize == 2) return ttc_pass::launch<Tin, unsigned short>(p, npairs, s);
+    return ttc_pass::launch<Tin, float>(p, npairs, s);
 }
 
 // all levels of npairs pairs: pair p is (prev + p * pair_stride, cur + p * pair_stride);
@@ -359,10 +359,11 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
         p.write_prev = independent;
         const int in_es = g.esize[l];
         cudaError_t e;
-        const int vec = l == 0 ? vec0 : 1;
-        if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, l, vec, npairs, s);
-        else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es, l, vec, npairs, s);
-        else e = launch_pass<float>(p, out_es, l, vec, npairs, s);
+        p.vec = l == 0 ? vec0 : 1;
+        p.padded = l == 0 ? 0 : 1;
+        if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, npairs, s);
+        else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es, npairs, s);
+        else e = launch_pass<float>(p, out_es, npairs, s);
         if (e != cudaSuccess) {
             ft::set_cuda_error(e);
             return FT_ERR_CUDA;

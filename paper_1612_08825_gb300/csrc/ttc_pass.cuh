@@ -35,7 +35,7 @@ constexpr int NSUM = 10;
 #endif
 
 // tile sets of one launch
-enum TileSet { SET_INTERIOR = 0, SET_BOTTOM = 1, SET_RIGHT = 2, SET_EDGES = 3, SET_ALL = 4 };
+enum TileSet { SET_INTERIOR = 0, SET_EDGES = 1, SET_BOTTOM = 2, SET_RIGHT = 3, SET_ALL = 4 };
 
 struct PassParams {
     const unsigned char *prev;  // level-l image, first frame of pair 0
@@ -45,6 +45,8 @@ struct PassParams {
     int H, W;                   // level-l image size
     int tiles_x, tiles_y, ntiles;
     int set;                    // which tiles this launch covers (TileSet)
+    int vec;                    // 1: rows allow vector loads
+    int padded;                 // 1: images padded past the last tile (context images)
     float xoff, yoff;           // cube centre: x = j + xoff, y = i + yoff
     float *partials;            // this level: [pair][tile][NSUM]
     unsigned char *next;        // level-(l+1) image of frame 0, or null
@@ -158,8 +160,11 @@ template <typename T> struct RawRow {
     float a4, b4;
 };
 
-__device__ __forceinline__ uint32_t load4_checked(const unsigned char *row, int col, int W, bool rowok)
+// element loads with bounds checks; whole groups inside the row use one vector load
+// (vec: the rows allow it)
+__device__ __forceinline__ uint32_t load4_checked(const unsigned char *row, int col, int W, bool rowok, int vec)
 {
+    if (vec && rowok && col + 4 <= W) return __ldg(reinterpret_cast<const unsigned int *>(row + col));
     uint32_t w = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -169,8 +174,9 @@ __device__ __forceinline__ uint32_t load4_checked(const unsigned char *row, int 
     }
     return w;
 }
-__device__ __forceinline__ uint2 load4_checked(const unsigned short *row, int col, int W, bool rowok)
+__device__ __forceinline__ uint2 load4_checked(const unsigned short *row, int col, int W, bool rowok, int vec)
 {
+    if (vec && rowok && col + 4 <= W) return __ldg(reinterpret_cast<const uint2 *>(row + col));
     uint32_t v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -180,8 +186,9 @@ __device__ __forceinline__ uint2 load4_checked(const unsigned short *row, int co
     }
     return make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
 }
-__device__ __forceinline__ float4 load4_checked(const float *row, int col, int W, bool rowok)
+__device__ __forceinline__ float4 load4_checked(const float *row, int col, int W, bool rowok, int vec)
 {
+    if (vec && rowok && col + 4 <= W) return __ldg(reinterpret_cast<const float4 *>(row + col));
     float v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -210,10 +217,10 @@ __device__ __forceinline__ void load_raw(const PassParams &p, const T *fa, const
         r.bl = rowok ? bl : z;
         r.br = rowok ? br : z;
     } else {
-        r.al = load4_checked(ra, gcl, p.W, rowok);
-        r.ar = load4_checked(ra, gcr, p.W, rowok);
-        r.bl = load4_checked(rb, gcl, p.W, rowok);
-        r.br = load4_checked(rb, gcr, p.W, rowok);
+        r.al = load4_checked(ra, gcl, p.W, rowok, p.vec);
+        r.ar = load4_checked(ra, gcr, p.W, rowok, p.vec);
+        r.bl = load4_checked(rb, gcl, p.W, rowok, p.vec);
+        r.br = load4_checked(rb, gcr, p.W, rowok, p.vec);
     }
     const int c4 = gcr + 4;
     const bool ok4 = rowok && (!COLCHK || c4 < p.W);
@@ -257,10 +264,10 @@ __device__ __forceinline__ void mask3(float2 &ex, float2 &ey, float2 &et, bool o
 // One row step: previous row (ps = prev + cur, pd = cur - prev, per column) and the
 // current row A (prev frame), B (cur frame) give the 4 cube pairs of the previous
 // row.  Columns are streamed left to right (two-column window of intermediates).
-template <bool EDGE>
+template <bool MASK>
 __device__ __forceinline__ void strip_row(const float2 A[5], const float2 B[5], float2 ps[5], float2 pd[5],
                                           bool first, float2 x0, float yv, bool rowok, int jl, int jr,
-                                          int Wlim, float2 acc[NSUM])
+                                          int jlo, int jhi, float2 acc[NSUM])
 {
     const float2 y = make_float2(yv, yv);
     float2 cs_p, vd_p, td_p;
@@ -276,7 +283,10 @@ __device__ __forceinline__ void strip_row(const float2 A[5], const float2 B[5], 
                 float2 ex = sub2(cs, cs_p);
                 float2 ey = add2(vd_p, vd);
                 float2 et = add2(td_p, td);
-                if (EDGE) mask3(ex, ey, et, rowok && (jl + k - 1 < Wlim), rowok && (jr + k - 1 < Wlim));
+                if (MASK) {
+                    const int cl = jl + k - 1, cr = jr + k - 1;
+                    mask3(ex, ey, et, rowok && cl >= jlo && cl < jhi, rowok && cr >= jlo && cr < jhi);
+                }
                 const float kk = (float)(k - 1);
                 accum2(acc, ex, ey, et, add2(x0, make_float2(kk, kk)), y);
             }
@@ -311,9 +321,11 @@ __device__ __forceinline__ void store_next(unsigned char *img, int64_t pitch, in
     }
 }
 
+// R0, C0: first cube row / column the tile reads; cubes outside [ilo, ihi) x [jlo, jhi)
+// are masked (MASK only)
 template <typename Tin, typename Tout, bool ROWCHK, bool COLCHK, bool MASK, bool WRITE>
 __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, const Tin *fb, int pair, int R0,
-                                          int C0, float2 acc[NSUM])
+                                          int C0, int ilo, int ihi, int jlo, int jhi, float2 acc[NSUM])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gcl = C0 + 4 * lane;
@@ -340,7 +352,8 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
         float2 A[5], B[5];
         unpack5(raw[r], lane, A, B);
         const int i = gr0 + r - 1;
-        strip_row<MASK>(A, B, ps, pd, r == 0, x0, (float)i + p.yoff, i < p.H - 1, gcl, gcl + HALF, p.W - 1, acc);
+        strip_row<MASK>(A, B, ps, pd, r == 0, x0, (float)i + p.yoff, i >= ilo && i < ihi, gcl, gcl + HALF, jlo,
+                        jhi, acc);
         if (WRITE && r < 8) {
             if ((r & 1) == 0) {
                 ha[0] = add2(A[0], A[1]); ha[1] = add2(A[2], A[3]);
@@ -363,31 +376,37 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
     }
 }
 
-// Tile sets and checks.  Interior tiles read only inside the image: vector loads, no
-// masks.  The bottom tile row of a level-0 frame clamps rows past the image (columns
-// stay inside).  The right tile column of a level-0 frame checks every element.  The
-// images of levels >= 1 are padded by the context so that every tile reads inside its
-// allocation: their edge tiles use vector loads and only mask the cubes.
+// Tile sets.  Interior tiles read only inside the image: vector loads, no masks.
+// Images of levels >= 1 live in the context, padded past the last tile row and
+// column: their last tile row and column (SET_EDGES) are shifted inwards (origin
+// H - 1 - TR rounded up to even, W - 1 - TC rounded up to a multiple of 4) so that
+// they cover the rest of the image with vector loads, read at most one row and three
+// columns into the padding, and mask every cube outside their own tile or the image;
+// pyramid pixels they share with a neighbour are written twice with the same value.
+// Level 0 reads the caller's frames, which have no padding: its last tile row clamps
+// rows past the image (SET_BOTTOM; vector loads, columns inside), its last tile
+// column checks every element group (SET_RIGHT), and SET_ALL (narrow images or
+// frames whose rows do not allow vector loads) checks everything.
 __device__ __forceinline__ void decode_tile(const PassParams &p, int64_t bid, int &pair, int &ty, int &tx)
 {
     int n;
     switch (p.set) {
     case SET_INTERIOR: n = (p.tiles_y - 1) * (p.tiles_x - 1); break;
+    case SET_EDGES: n = p.tiles_x + p.tiles_y - 1; break;
     case SET_BOTTOM: n = p.tiles_x - 1; break;
     case SET_RIGHT: n = p.tiles_y; break;
-    case SET_EDGES: n = p.tiles_x + p.tiles_y - 1; break;
     default: n = p.ntiles; break;
     }
     pair = (int)(bid / n);
     const int t = (int)(bid - (int64_t)pair * n);
     switch (p.set) {
     case SET_INTERIOR: ty = t / (p.tiles_x - 1); tx = t - ty * (p.tiles_x - 1); break;
-    case SET_BOTTOM: ty = p.tiles_y - 1; tx = t; break;
-    case SET_RIGHT: ty = t; tx = p.tiles_x - 1; break;
     case SET_EDGES:
         if (t < p.tiles_x) { ty = p.tiles_y - 1; tx = t; }
         else { ty = t - p.tiles_x; tx = p.tiles_x - 1; }
         break;
+    case SET_BOTTOM: ty = p.tiles_y - 1; tx = t; break;
+    case SET_RIGHT: ty = t; tx = p.tiles_x - 1; break;
     default: ty = t / p.tiles_x; tx = t - ty * p.tiles_x; break;
     }
 }
@@ -396,14 +415,16 @@ inline int64_t set_size(const PassParams &p)
 {
     switch (p.set) {
     case SET_INTERIOR: return (int64_t)(p.tiles_y - 1) * (p.tiles_x - 1);
+    case SET_EDGES: return p.tiles_x + p.tiles_y - 1;
     case SET_BOTTOM: return p.tiles_x - 1;
     case SET_RIGHT: return p.tiles_y;
-    case SET_EDGES: return p.tiles_x + p.tiles_y - 1;
     default: return p.ntiles;
     }
 }
 
-template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK>
+// ROWCHK / COLCHK: bounds checks on rows / element groups; MASK: cubes outside the
+// tile or the image are masked; SHIFT: edge tiles move inwards (padded images)
+template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK, bool SHIFT>
 __global__ void __launch_bounds__(NT, FT_TTC_MINB)
 ttc_pass_kernel(const PassParams p)
 {
@@ -411,51 +432,55 @@ ttc_pass_kernel(const PassParams p)
     int pair, ty, tx;
     decode_tile(p, blockIdx.x, pair, ty, tx);
     const int tile = ty * p.tiles_x + tx;
-    const int R0 = ty * TR, C0 = tx * TC;
+    const int ilo = ty * TR, jlo = tx * TC;
+    int R0 = ilo, C0 = jlo;
+    if (SHIFT) {
+        R0 = min(R0, (p.H - 1 - TR + 1) & ~1);
+        C0 = min(C0, (p.W - 1 - TC + 3) & ~3);
+    }
     const Tin *fa = reinterpret_cast<const Tin *>(p.prev + (int64_t)pair * p.pair_stride);
     const Tin *fb = reinterpret_cast<const Tin *>(p.cur + (int64_t)pair * p.pair_stride);
 
     float2 acc2[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc2[s] = make_float2(0.f, 0.f);
-    pass_body<Tin, Tout, ROWCHK, COLCHK, MASK, WRITE>(p, fa, fb, pair, R0, C0, acc2);
+    pass_body<Tin, Tout, ROWCHK, COLCHK, MASK, WRITE>(p, fa, fb, pair, R0, C0, ilo, min(ilo + TR, p.H - 1), jlo,
+                                                      min(jlo + TC, p.W - 1), acc2);
     float acc[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc[s] = acc2[s].x + acc2[s].y;
     block_reduce(acc, red, p.partials + ((int64_t)pair * p.ntiles + tile) * NSUM);
 }
 
-template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK>
+template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK, bool SHIFT>
 void launch_set(PassParams p, int set, int npairs, cudaStream_t s)
 {
     p.set = set;
     const int64_t n = set_size(p) * npairs;
-    if (n > 0) ttc_pass_kernel<Tin, Tout, WRITE, ROWCHK, COLCHK, MASK><<<(unsigned)n, NT, 0, s>>>(p);
+    if (n > 0) ttc_pass_kernel<Tin, Tout, WRITE, ROWCHK, COLCHK, MASK, SHIFT><<<(unsigned)n, NT, 0, s>>>(p);
 }
 
-// level: 0 reads the caller's frames (vec: rows allow vector loads), >= 1 the padded
-// context images
 template <typename Tin, typename Tout, bool WRITE>
-cudaError_t launch_w(const PassParams &p, int level, int vec, int npairs, cudaStream_t s)
+cudaError_t launch_w(const PassParams &p, int npairs, cudaStream_t s)
 {
-    if (level > 0) {
-        launch_set<Tin, Tout, WRITE, false, false, false>(p, SET_INTERIOR, npairs, s);
-        launch_set<Tin, Tout, WRITE, false, false, true>(p, SET_EDGES, npairs, s);
-    } else if (vec) {
-        launch_set<Tin, Tout, WRITE, false, false, false>(p, SET_INTERIOR, npairs, s);
-        launch_set<Tin, Tout, WRITE, true, false, true>(p, SET_BOTTOM, npairs, s);
-        launch_set<Tin, Tout, WRITE, true, true, true>(p, SET_RIGHT, npairs, s);
+    const bool big = p.H >= TR + 2 && p.W >= TC + 4;
+    if (p.padded && big) {
+        launch_set<Tin, Tout, WRITE, false, false, false, false>(p, SET_INTERIOR, npairs, s);
+        launch_set<Tin, Tout, WRITE, false, false, true, true>(p, SET_EDGES, npairs, s);
+    } else if (p.vec && big) {
+        launch_set<Tin, Tout, WRITE, false, false, false, false>(p, SET_INTERIOR, npairs, s);
+        launch_set<Tin, Tout, WRITE, true, false, true, false>(p, SET_BOTTOM, npairs, s);
+        launch_set<Tin, Tout, WRITE, true, true, true, false>(p, SET_RIGHT, npairs, s);
     } else {
-        launch_set<Tin, Tout, WRITE, true, true, true>(p, SET_ALL, npairs, s);
+        launch_set<Tin, Tout, WRITE, true, true, true, false>(p, SET_ALL, npairs, s);
     }
     return cudaGetLastError();
 }
 
 template <typename Tin, typename Tout>
-cudaError_t launch(const PassParams &p, int level, int vec, int npairs, cudaStream_t s)
+cudaError_t launch(const PassParams &p, int npairs, cudaStream_t s)
 {
-    return p.next ? launch_w<Tin, Tout, true>(p, level, vec, npairs, s)
-                  : launch_w<Tin, Tout, false>(p, level, vec, npairs, s);
+    return p.next ? launch_w<Tin, Tout, true>(p, npairs, s) : launch_w<Tin, Tout, false>(p, npairs, s);
 }
 
 }  // namespace ttc_pass
