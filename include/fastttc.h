@@ -164,6 +164,30 @@ ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, int dtype, 
                     void *stream);
 
 /*
+ * ttc_solve for one frame pair without allocating any device memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * after start-up -- hard real-time control loops (an allocation can block for an
+ * unbounded time), safety-certified vehicle software that forbids dynamic allocation,
+ * and plug-ins whose host process owns all device memory through its own allocator.
+ * The caller still passes and owns prev, cur and out (same meaning, layout and
+ * results as ttc_solve, in place of a context).
+ *
+ * Scratch: a fixed array of FT_NOALLOC_SCRATCH_BYTES in the library's device memory,
+ * held by every GPU that loads the library until the process exits.  It covers any
+ * single pair up to 1920 x 1080 with up to FT_MAX_LEVELS levels in either dtype;
+ * larger requests are rejected with FT_ERR_WORKSPACE before anything is launched.
+ * The first call on a device looks up the array's device address for that device
+ * (with that device current); make that first call before any stream capture.
+ * Every call uses the same array and leaves the last call's contents in it: nothing
+ * there needs to start at zero (each call writes every value it reads), but calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on it, so
+ * serialise them.  Errors: as ttc_solve, plus FT_ERR_WORKSPACE for oversized requests.
+ */
+#define FT_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dtype, int H, int W, int64_t pitch_bytes,
+                            int levels, int mode, ttc_level_result *out, void *stream);
+
+/*
  * The same for the T-1 consecutive pairs (t, t+1) of a video of T frames stored
  * frame_stride_bytes apart: out[(t * levels) + l] for pair t, level l (device,
  * (T-1) * levels results).  Sec. V-B: the estimate is produced at every frame.

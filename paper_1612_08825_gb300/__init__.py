@@ -20,7 +20,7 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "ttc_derivatives",
+    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "ttc_derivatives", "ttc_solve_noalloc",
     "TtcContext", "RESULT_DTYPE", "results_to_numpy", "select_level",
     "MODE_TTC", "MODE_FOE", "FLAG_SINGULAR", "FLAG_C_ZERO", "FLAG_RECEDING", "MAX_LEVELS",
     "MAX_NDIM",
@@ -90,6 +90,9 @@ def load(path: Optional[str] = None):
     L.ttc_solve.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                             ctypes.c_int, ctypes.c_int, _vp, _vp]
     L.ttc_solve.restype = st
+    L.ttc_solve_noalloc.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                    ctypes.c_int, ctypes.c_int, _vp, _vp]
+    L.ttc_solve_noalloc.restype = st
     L.ttc_solve_sequence.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _vp, _vp]
     L.ttc_solve_sequence.restype = st
@@ -209,6 +212,29 @@ def select_level(results: np.ndarray, rule: int = 0) -> int:
     if v == -2:
         raise ValueError("invalid arguments to ttc_select_level")
     return int(v)
+
+
+def ttc_solve_noalloc(prev: torch.Tensor, cur: torch.Tensor, levels: int = 1, mode: int = MODE_FOE,
+                      out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """One frame pair through ttc_solve_noalloc (library allocates no device memory).
+
+    For callers that cannot allocate device memory once running; the library's fixed
+    scratch array is shared by all calls, so calls must not overlap on the GPU.
+    """
+    L = load()
+    _require_cuda(prev, "prev")
+    _require_cuda(cur, "cur")
+    if prev.shape != cur.shape or prev.dtype != cur.dtype or prev.dim() != 2:
+        raise ValueError("prev and cur must be 2-D tensors of one shape and dtype")
+    if prev.stride(1) != 1 or cur.stride(1) != 1 or prev.stride(0) != cur.stride(0):
+        raise ValueError("rows must be contiguous with one common pitch")
+    dt, es = _frame_args(prev)
+    H, W = prev.shape
+    if out is None:
+        out = torch.empty(levels * RESULT_DTYPE.itemsize, dtype=torch.uint8, device=prev.device)
+    _check(L.ttc_solve_noalloc(prev.data_ptr(), cur.data_ptr(), dt, H, W, prev.stride(0) * es, int(levels),
+                               int(mode), out.data_ptr(), _stream_ptr(prev)), "ttc_solve_noalloc")
+    return out
 
 
 class TtcContext:

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -424,6 +425,77 @@ extern "C" ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, 
                                    ft::as_stream(stream));
     if (st != FT_OK) return st;
     return launch_solve(ctx, mode, out, ft::as_stream(stream));
+}
+
+// ---------------------------------------------------------------------------
+// ttc_solve without device allocation: scratch in a fixed static device array
+// ---------------------------------------------------------------------------
+
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[FT_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device (looked up once per
+// device; in host code the array's name is only a host-side stand-in).
+ft_status noalloc_scratch(unsigned char **base)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return FT_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            ft::set_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+            return FT_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = ptr;
+    }
+    *base = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    return FT_OK;
+}
+
+}  // namespace
+
+extern "C" ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dtype, int H, int W,
+                                       int64_t pitch_bytes, int levels, int mode, ttc_level_result *out,
+                                       void *stream)
+{
+    if (!prev || !cur || !out) return FT_ERR_INVALID_ARG;
+    if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
+    ft_status st = check_frames(dtype, H, W, pitch_bytes);
+    if (st != FT_OK) return st;
+    if ((st = check_levels(H, W, levels)) != FT_OK) return st;
+    Geometry g;
+    geometry(H, W, levels, dtype, 1, 2, g);
+    const int64_t pbytes = (g.partial_floats * (int64_t)sizeof(float) + 255) / 256 * 256;
+    if (pbytes + g.image_bytes > (int64_t)FT_NOALLOC_SCRATCH_BYTES) return FT_ERR_WORKSPACE;
+    unsigned char *base = nullptr;
+    if ((st = noalloc_scratch(&base)) != FT_OK) return st;
+    // a context on the stack whose workspace is the static array
+    ttc_ctx c{};
+    c.max_H = H;
+    c.max_W = W;
+    c.max_levels = levels;
+    c.max_pairs = 1;
+    c.partials = reinterpret_cast<float *>(base);
+    c.images = base + pbytes;
+    c.partial_cap = g.partial_floats;
+    c.image_cap = g.image_bytes;
+    c.bytes = FT_NOALLOC_SCRATCH_BYTES;
+    c.ready = false;
+    st = launch_partials(&c, prev, cur, 0, 1, 0, dtype, H, W, pitch_bytes, levels, ft::as_stream(stream));
+    if (st != FT_OK) return st;
+    return launch_solve(&c, mode, out, ft::as_stream(stream));
 }
 
 extern "C" ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
