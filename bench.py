@@ -86,7 +86,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -168,13 +168,16 @@ def fastconv_sweep(dev, hbm_peak, reps):
     import scenes
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     rows = []
+    # the sweep's shapes, plus batches of 16 images (a leading extent-1 kernel axis)
+    # that show the sustained bandwidth of the memory-bound kernels
     cases = [((1080, 1920), (k, k), "gauss") for k in (2, 3, 7, 15)] + \
-            [((64, 256, 256), (k, k, k), "normal") for k in (2, 5)]
+            [((64, 256, 256), (k, k, k), "normal") for k in (2, 5)] + \
+            [((16, 1080, 1920), (1, k, k), "gauss") for k in (2, 3)]
     launches = 0
     for shape, kshape, kind in cases:
         E = torch.from_numpy(scenes.uniform_array(shape, seed=2024)).to(dev)
         if kind == "gauss":
-            k = torch.from_numpy(scenes.gaussian_kernel(kshape[0])).to(dev)
+            k = torch.from_numpy(scenes.gaussian_kernel(kshape[-1]).reshape(kshape)).to(dev)
         else:
             k = torch.from_numpy(scenes.normal_array(kshape, seed=78)).to(dev)
         out = ft.fastconv_nd(E, k)
@@ -225,6 +228,13 @@ def accuracy(sc, res, levels):
     return out
 
 
+# FP32 lane-operations the method needs per level-0 cube in this formulation (Sec. II,
+# V-A): exact float of the two new pixels (2), per-column sums/differences (2 + 3),
+# Ex/Ey/Et (3), G (2), the ten products (10), plus the next pyramid level (2x2 block
+# sums of both frames: 6 adds per 4 level-0 pixels = 1.5)
+OPS_PER_CUBE0 = 23.5
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -241,6 +251,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     ft.load()
     hbm_peak, sm_max, peak_src = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    alu_peak = n_sm * 128 * sm_max * 1e6          # FP32 lane-ops/s at the maximum SM clock
 
     frames_n = args.frames
     npairs = frames_n - 1
@@ -251,19 +264,20 @@ def run_ours(args):
     out = ctx.new_results(npairs * LEVELS)
     s = torch.cuda.current_stream(dev)
 
-    def step(evs=None):
-        if evs is not None:
-            evs[0].record(s)
+    def step():
         ctx.partial_sums(frames, levels=LEVELS)
-        if evs is not None:
-            evs[1].record(s)
         ctx.reduce_solve(out, mode=ft.MODE_FOE)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
+    launches_per_step = ctx.last_launch_count + 1
 
+    # level-0 pass timing: events recorded by the library around its launches
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    for a, b in ev:
+        a.record(s)
+        b.record(s)
     clocks = ClockSampler(_smi_index(local))
     clocks.start()
     time.sleep(0.3)
@@ -274,14 +288,16 @@ def run_ours(args):
     end = torch.cuda.Event(enable_timing=True)
     start.record(s)
     for i in range(args.steps):
-        step(ev[i])
+        ctx.set_level0_events(ev[i][0], ev[i][1])
+        step()
     end.record(s)
     torch.cuda.synchronize(dev)
+    ctx.set_level0_events(None, None)
     if world > 1:
         dist.barrier()
     ck = clocks.stop()
     elapsed = start.elapsed_time(end) * 1e-3
-    tile_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    l0_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     t_all = torch.tensor([elapsed], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
@@ -290,7 +306,8 @@ def run_ours(args):
 
     res = ft.results_to_numpy(out).reshape(npairs, LEVELS)
 
-    # parity spot check of the timed results against the oracle (rank 0, two pairs)
+    # parity spot check of the timed results and the CPU baseline (rank 0): the oracle
+    # on the first pairs of the same video, one host core, bounded time
     parity = None
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -313,7 +330,8 @@ def run_ours(args):
                "sample": f"first {n_done} pairs of the same video, 5 levels, FOE, single thread"}
         parity = {"pairs_checked": n_done, "max_sum_err_rel_abssum": worst, "tolerance": 1e-5}
 
-    # e2e through the public API with pinned host frames
+    # e2e through the public API with pinned host frames: H2D of the video, both
+    # stages, D2H of the result records, every step
     e2e = None
     if not args.no_e2e:
         host_frames = frames.cpu().pin_memory()
@@ -321,7 +339,7 @@ def run_ours(args):
         for _ in range(2):
             ctx.solve_sequence(host_frames, levels=LEVELS, mode=ft.MODE_FOE, out=hout)
         torch.cuda.synchronize(dev)
-        k2 = max(2, args.steps // 2)
+        k2 = max(3, args.steps // 4)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         if world > 1:
@@ -336,30 +354,40 @@ def run_ours(args):
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": npairs * k2 * world / float(te.item()), "unit": UNIT,
-               "h2d_bytes_per_step": int(host_frames.numel()), "d2h_bytes_per_step": int(hout.numel())}
+               "h2d_bytes_per_step": int(host_frames.numel()), "d2h_bytes_per_step": int(hout.numel()),
+               "steps": k2}
         e2e_res = ft.results_to_numpy(hout).reshape(npairs, LEVELS)
         assert e2e_res.tobytes() == res.tobytes(), "host-buffer path disagrees with device path"
 
-    conv_rows, conv_launches = (None, 0)
+    conv_rows = None
     if rank == 0 and not args.no_conv:
-        conv_rows, conv_launches = fastconv_sweep(dev, hbm_peak, reps=args.conv_reps)
+        conv_rows, _ = fastconv_sweep(dev, hbm_peak, reps=args.conv_reps)
 
     if rank == 0:
-        # every frame of the video read once + the result records written
-        algo_bytes = frames_n * H * W + npairs * LEVELS * ft.RESULT_DTYPE.itemsize
-        achieved = algo_bytes / (tile_ms * 1e-3) / 1e9
+        cubes0 = (H - 1) * (W - 1) * npairs
+        achieved_ops = cubes0 * OPS_PER_CUBE0 / (l0_ms * 1e-3)
+        # level-0 pass bytes: every frame read once, the level-1 images written
+        # (uint16), the tile partials written
+        l0_bytes = frames_n * H * W + frames_n * (H // 2) * (W // 2) * 2 + npairs * (-(-(H - 1) // 64)) * (-(-(W - 1) // 256)) * 10 * 4
+        step_bytes = frames_n * H * W + npairs * LEVELS * ft.RESULT_DTYPE.itemsize
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": _config(frames_n),
-            "roofline": {"kernel": "ttc_tile_kernel<u8>", "bound": "hbm", "achieved": achieved,
-                         "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "traffic": None, "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": tile_ms},
+            "roofline": {"kernel": "ttc level-0 pass (ttc_pass_kernel<u8>, interior + edge launches)",
+                         "bound": "alu", "achieved": achieved_ops / 1e12, "peak": alu_peak / 1e12,
+                         "unit": "TFP32-lane-op/s", "frac": achieved_ops / alu_peak, "traffic": None,
+                         "ops_per_cube": OPS_PER_CUBE0, "cubes_per_launch": cubes0, "launch_ms": l0_ms,
+                         "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
+                         "hbm": {"achieved": l0_bytes / (l0_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": l0_bytes / (l0_ms * 1e-3) / 1e9 / hbm_peak, "bytes": l0_bytes}},
+            "step_hbm": {"algorithmic_bytes": step_bytes, "GBps": step_bytes / (tmax / args.steps) / 1e9,
+                         "frac": step_bytes / (tmax / args.steps) / 1e9 / hbm_peak},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": launches_per_step * args.steps,
+            "launches_per_step": launches_per_step,
             "clocks": ck,
             "parity": parity,
             "accuracy": accuracy(sc, res, LEVELS),
@@ -375,7 +403,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=T_FRAMES)

@@ -208,6 +208,18 @@ ft_status ttc_partial_sums(ttc_ctx *ctx, const void *frames, int64_t frame_strid
 ft_status ttc_reduce_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, void *stream);
 
 /*
+ * Timing hook (no counterpart in the paper): when start and end are non-null
+ * (cudaEvent_t values passed as void*), every later ttc_partial_sums /
+ * ttc_solve_sequence / ttc_solve on this context records `start` on its stream just
+ * before the launches of the level-0 pass and `end` just after them, so that a
+ * caller can time the dominant pass alone.  NULL, NULL turns it off.
+ * Errors: FT_ERR_INVALID_ARG (null context, or exactly one event null).
+ */
+ft_status ttc_ctx_set_level0_events(ttc_ctx *ctx, void *start, void *end);
+/* Number of kernels the last ttc_partial_sums on this context launched (0 before any). */
+int ttc_ctx_last_launch_count(const ttc_ctx *ctx);
+
+/*
  * Multi-scale selection (Sec. V-B), host only: start at the finest usable level
  * and move one level coarser while the next level is usable and its key is
  * smaller ("improved (ie. reduced)"); rule 0: key = TTC; rule 1: key = resid.

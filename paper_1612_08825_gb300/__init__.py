@@ -101,6 +101,10 @@ def load(path: Optional[str] = None):
     L.ttc_partial_sums.restype = st
     L.ttc_reduce_solve.argtypes = [_vp, ctypes.c_int, _vp, _vp]
     L.ttc_reduce_solve.restype = st
+    L.ttc_ctx_set_level0_events.argtypes = [_vp, _vp, _vp]
+    L.ttc_ctx_set_level0_events.restype = st
+    L.ttc_ctx_last_launch_count.argtypes = [_vp]
+    L.ttc_ctx_last_launch_count.restype = ctypes.c_int
     L.ttc_select_level.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.ttc_select_level.restype = ctypes.c_int
     _lib = L
@@ -265,6 +269,18 @@ class TtcContext:
             self.close()
         except Exception:
             pass
+
+    def set_level0_events(self, start: Optional[torch.cuda.Event], end: Optional[torch.cuda.Event]):
+        """Record `start`/`end` around the level-0 pass of later calls (None, None: off)."""
+        L = load()
+        sp = start.cuda_event if start is not None else None
+        ep = end.cuda_event if end is not None else None
+        _check(L.ttc_ctx_set_level0_events(self._h, sp, ep), "ttc_ctx_set_level0_events")
+
+    @property
+    def last_launch_count(self) -> int:
+        """Kernels launched by the last partial-sums stage (the merge/solve adds one)."""
+        return int(load().ttc_ctx_last_launch_count(self._h))
 
     def new_results(self, n: int) -> torch.Tensor:
         return torch.empty(n * RESULT_DTYPE.itemsize, dtype=torch.uint8, device=self.device)

@@ -241,6 +241,8 @@ struct ttc_ctx {
     size_t bytes;
     Geometry g;               // of the last ttc_partial_sums call
     bool ready;
+    cudaEvent_t ev0_start, ev0_end;   // optional timing of the level-0 pass
+    int launches;                     // kernels launched by the last ttc_partial_sums
 };
 
 extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max_levels, int max_pairs)
@@ -296,13 +298,23 @@ extern "C" void ttc_ctx_destroy(ttc_ctx *ctx)
 
 extern "C" size_t ttc_ctx_workspace_bytes(const ttc_ctx *ctx) { return ctx ? ctx->bytes : 0; }
 
+extern "C" int ttc_ctx_last_launch_count(const ttc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" ft_status ttc_ctx_set_level0_events(ttc_ctx *ctx, void *start, void *end)
+{
+    if (!ctx || (!start) != (!end)) return FT_ERR_INVALID_ARG;
+    ctx->ev0_start = static_cast<cudaEvent_t>(start);
+    ctx->ev0_end = static_cast<cudaEvent_t>(end);
+    return FT_OK;
+}
+
 namespace {
 
 template <typename Tin>
-cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs, cudaStream_t s)
+cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs, cudaStream_t s, int *count)
 {
-    if (out_esize == 2) return ttc_pass::launch<Tin, unsigned short>(p, npairs, s);
-    return ttc_pass::launch<Tin, float>(p, npairs, s);
+    if (out_esize == 2) return ttc_pass::launch<Tin, unsigned short>(p, npairs, s, count);
+    return ttc_pass::launch<Tin, float>(p, npairs, s, count);
 }
 
 // all levels of npairs pairs: pair p is (prev + p * pair_stride, cur + p * pair_stride);
@@ -323,6 +335,7 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
     for (int l = 0; l < levels; ++l)
         if ((int64_t)npairs * g.ntiles[l] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
 
+    int launches = 0;
     const uintptr_t al = dtype == FT_U8 ? 3 : 15;
     const int vec0 = ((reinterpret_cast<uintptr_t>(prev) & al) == 0 && (reinterpret_cast<uintptr_t>(cur) & al) == 0 &&
                       (pitch & (int64_t)al) == 0 && (pair_stride & (int64_t)al) == 0) ? 1 : 0;
@@ -359,12 +372,18 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
         }
         p.write_prev = independent;
         const int in_es = g.esize[l];
-        cudaError_t e;
+        cudaError_t e = cudaSuccess;
+        if (l == 0 && ctx->ev0_start) e = cudaEventRecord(ctx->ev0_start, s);
+        if (e != cudaSuccess) {
+            ft::set_cuda_error(e);
+            return FT_ERR_CUDA;
+        }
         p.vec = l == 0 ? vec0 : 1;
         p.padded = l == 0 ? 0 : 1;
-        if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, npairs, s);
-        else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es, npairs, s);
-        else e = launch_pass<float>(p, out_es, npairs, s);
+        if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, npairs, s, &launches);
+        else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es, npairs, s, &launches);
+        else e = launch_pass<float>(p, out_es, npairs, s, &launches);
+        if (e == cudaSuccess && l == 0 && ctx->ev0_end) e = cudaEventRecord(ctx->ev0_end, s);
         if (e != cudaSuccess) {
             ft::set_cuda_error(e);
             return FT_ERR_CUDA;
@@ -372,6 +391,7 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
     }
     ctx->g = g;
     ctx->ready = true;
+    ctx->launches = launches;
     return FT_OK;
 }
 

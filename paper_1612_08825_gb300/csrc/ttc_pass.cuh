@@ -453,34 +453,39 @@ ttc_pass_kernel(const PassParams p)
 }
 
 template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK, bool SHIFT>
-void launch_set(PassParams p, int set, int npairs, cudaStream_t s)
+int launch_set(PassParams p, int set, int npairs, cudaStream_t s)
 {
     p.set = set;
     const int64_t n = set_size(p) * npairs;
-    if (n > 0) ttc_pass_kernel<Tin, Tout, WRITE, ROWCHK, COLCHK, MASK, SHIFT><<<(unsigned)n, NT, 0, s>>>(p);
+    if (n <= 0) return 0;
+    ttc_pass_kernel<Tin, Tout, WRITE, ROWCHK, COLCHK, MASK, SHIFT><<<(unsigned)n, NT, 0, s>>>(p);
+    return 1;
 }
 
+// launches the pass; adds the number of kernels launched to *count
 template <typename Tin, typename Tout, bool WRITE>
-cudaError_t launch_w(const PassParams &p, int npairs, cudaStream_t s)
+cudaError_t launch_w(const PassParams &p, int npairs, cudaStream_t s, int *count)
 {
     const bool big = p.H >= TR + 2 && p.W >= TC + 4;
+    int n = 0;
     if (p.padded && big) {
-        launch_set<Tin, Tout, WRITE, false, false, false, false>(p, SET_INTERIOR, npairs, s);
-        launch_set<Tin, Tout, WRITE, false, false, true, true>(p, SET_EDGES, npairs, s);
+        n += launch_set<Tin, Tout, WRITE, false, false, false, false>(p, SET_INTERIOR, npairs, s);
+        n += launch_set<Tin, Tout, WRITE, false, false, true, true>(p, SET_EDGES, npairs, s);
     } else if (p.vec && big) {
-        launch_set<Tin, Tout, WRITE, false, false, false, false>(p, SET_INTERIOR, npairs, s);
-        launch_set<Tin, Tout, WRITE, true, false, true, false>(p, SET_BOTTOM, npairs, s);
-        launch_set<Tin, Tout, WRITE, true, true, true, false>(p, SET_RIGHT, npairs, s);
+        n += launch_set<Tin, Tout, WRITE, false, false, false, false>(p, SET_INTERIOR, npairs, s);
+        n += launch_set<Tin, Tout, WRITE, true, false, true, false>(p, SET_BOTTOM, npairs, s);
+        n += launch_set<Tin, Tout, WRITE, true, true, true, false>(p, SET_RIGHT, npairs, s);
     } else {
-        launch_set<Tin, Tout, WRITE, true, true, true, false>(p, SET_ALL, npairs, s);
+        n += launch_set<Tin, Tout, WRITE, true, true, true, false>(p, SET_ALL, npairs, s);
     }
+    *count += n;
     return cudaGetLastError();
 }
 
 template <typename Tin, typename Tout>
-cudaError_t launch(const PassParams &p, int npairs, cudaStream_t s)
+cudaError_t launch(const PassParams &p, int npairs, cudaStream_t s, int *count)
 {
-    return p.next ? launch_w<Tin, Tout, true>(p, npairs, s) : launch_w<Tin, Tout, false>(p, npairs, s);
+    return p.next ? launch_w<Tin, Tout, true>(p, npairs, s, count) : launch_w<Tin, Tout, false>(p, npairs, s, count);
 }
 
 }  // namespace ttc_pass
