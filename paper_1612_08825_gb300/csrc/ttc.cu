@@ -7,6 +7,7 @@
 // partials in a fixed order, scaling to level-l mean-image units, and the FP64
 // solve of the normal equations (Eq. final_TTC).
 // Also here: the materialised level-0 derivatives, the context and the C ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,9 @@
 
 #include "common.cuh"
 #include "ttc_pass.cuh"
+#include "ttc_tma.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace {
 
@@ -33,6 +37,7 @@ struct SolveParams {
     int64_t poff[FT_MAX_LEVELS];      // level l partials start here: [pair][tile][NSUM]
     double inv_scale[FT_MAX_LEVELS];  // 1 / (16 * 16^l): level-l sums -> mean-image units
     int64_t ncubes[FT_MAX_LEVELS];
+    const int *status;                // nonzero: a stage-1 wait gave up
     ttc_level_result *out;
 };
 
@@ -129,6 +134,7 @@ ttc_solve_kernel(const SolveParams p)
         for (int s = 0; s < NSUM; ++s) r.sums[s] = acc[s] * p.inv_scale[l];
         r.n = p.ncubes[l];
         solve_one(r.sums, p.mode, l, &r);
+        if (*p.status) r.flags |= FT_FLAG_TIMEOUT;
         p.out[item] = r;
     }
 }
@@ -236,6 +242,7 @@ struct ttc_ctx {
     int max_H, max_W, max_levels, max_pairs;
     float *partials;
     unsigned char *images;
+    int *status;              // stage-1 timeout flag
     int64_t partial_cap;      // floats
     int64_t image_cap;        // bytes
     size_t bytes;
@@ -261,7 +268,8 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     const int64_t pf = g.partial_floats, ib = g.image_bytes;
     float *part = nullptr;
     unsigned char *img = nullptr;
-    cudaError_t e = cudaMalloc(&part, (size_t)pf * sizeof(float));
+    // the partials, then 256 bytes holding the status word
+    cudaError_t e = cudaMalloc(&part, (size_t)pf * sizeof(float) + 256);
     if (e == cudaSuccess && ib > 0) e = cudaMalloc(&img, (size_t)ib);
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
@@ -280,9 +288,10 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->max_pairs = max_pairs;
     c->partials = part;
     c->images = img;
+    c->status = reinterpret_cast<int *>(part + pf);
     c->partial_cap = pf;
     c->image_cap = ib;
-    c->bytes = (size_t)pf * sizeof(float) + (size_t)ib;
+    c->bytes = (size_t)pf * sizeof(float) + 256 + (size_t)ib;
     c->ready = false;
     *ctx = c;
     return FT_OK;
@@ -309,6 +318,79 @@ extern "C" ft_status ttc_ctx_set_level0_events(ttc_ctx *ctx, void *start, void *
 }
 
 namespace {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3-D map over npairs frames of H x W uint8 pixels (box: bw columns x TR+1 rows x 1)
+bool u8_frame_map(CUtensorMap *m, const void *base, int W, int H, int npairs, int64_t pitch, int64_t pstride,
+                  int bw)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)npairs};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pstride};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)(TR + 1), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// level 0 of uint8 frames by the persistent TMA kernel; false when the frames do not
+// meet the copy engine's alignment rules (the caller then uses the load path)
+bool launch_level0_tma(const ttc_pass::PassParams &p, const void *prev, const void *cur, int64_t pair_stride,
+                       int npairs, int *status, cudaStream_t s, cudaError_t *err)
+{
+    *err = cudaSuccess;
+    const int64_t pitch = p.pitch;
+    if ((reinterpret_cast<uintptr_t>(prev) & 15) || (reinterpret_cast<uintptr_t>(cur) & 15) || (pitch & 15))
+        return false;
+    int64_t ps = pair_stride;
+    if (npairs == 1) ps = (pitch * p.H + 15) / 16 * 16;
+    else if (ps <= 0 || (ps & 15)) return false;
+    CUtensorMap ma, mb, xa, xb;
+    if (!u8_frame_map(&ma, prev, p.W, p.H, npairs, pitch, ps, ttc_tma::BW) ||
+        !u8_frame_map(&mb, cur, p.W, p.H, npairs, pitch, ps, ttc_tma::BW) ||
+        !u8_frame_map(&xa, prev, p.W, p.H, npairs, pitch, ps, ttc_tma::XW) ||
+        !u8_frame_map(&xb, cur, p.W, p.H, npairs, pitch, ps, ttc_tma::XW))
+        return false;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    ttc_tma::TmaParams tp{};
+    tp.p = p;
+    tp.total = npairs * p.ntiles;
+    tp.status = status;
+    const int grid = std::min(tp.total, 2 * std::max(nsm, 1));
+    if (p.next) {
+        *err = cudaFuncSetAttribute(ttc_tma::ttc_pass_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    ttc_tma::SMEM);
+        if (*err == cudaSuccess)
+            ttc_tma::ttc_pass_tma_kernel<true><<<grid, ttc_pass::NT, ttc_tma::SMEM, s>>>(ma, mb, xa, xb, tp);
+    } else {
+        *err = cudaFuncSetAttribute(ttc_tma::ttc_pass_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    ttc_tma::SMEM);
+        if (*err == cudaSuccess)
+            ttc_tma::ttc_pass_tma_kernel<false><<<grid, ttc_pass::NT, ttc_tma::SMEM, s>>>(ma, mb, xa, xb, tp);
+    }
+    if (*err == cudaSuccess) *err = cudaGetLastError();
+    return true;
+}
 
 template <typename Tin>
 cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs, cudaStream_t s, int *count)
@@ -373,14 +455,21 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
         p.write_prev = independent;
         const int in_es = g.esize[l];
         cudaError_t e = cudaSuccess;
-        if (l == 0 && ctx->ev0_start) e = cudaEventRecord(ctx->ev0_start, s);
+        if (l == 0) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
+        if (e == cudaSuccess && l == 0 && ctx->ev0_start) e = cudaEventRecord(ctx->ev0_start, s);
         if (e != cudaSuccess) {
             ft::set_cuda_error(e);
             return FT_ERR_CUDA;
         }
         p.vec = l == 0 ? vec0 : 1;
         p.padded = l == 0 ? 0 : 1;
-        if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, npairs, s, &launches);
+        bool done = false;
+        if (l == 0 && dtype == FT_U8 && (out_es == 2 || !p.next)) {
+            done = launch_level0_tma(p, prev, cur, pair_stride, npairs, ctx->status, s, &e);
+            if (done) ++launches;
+        }
+        if (done) {
+        } else if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, npairs, s, &launches);
         else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es, npairs, s, &launches);
         else e = launch_pass<float>(p, out_es, npairs, s, &launches);
         if (e == cudaSuccess && l == 0 && ctx->ev0_end) e = cudaEventRecord(ctx->ev0_end, s);
@@ -412,6 +501,7 @@ ft_status launch_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream
         sp.inv_scale[l] = std::ldexp(1.0, -4 - 4 * l);
         sp.ncubes[l] = (int64_t)(g.H[l] - 1) * (int64_t)(g.W[l] - 1);
     }
+    sp.status = ctx->status;
     sp.out = out;
     ttc_solve_kernel<<<(unsigned)(g.npairs * g.levels), 32, 0, s>>>(sp);
     return ft::check_launch();
@@ -497,7 +587,8 @@ extern "C" ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dt
     if ((st = check_levels(H, W, levels)) != FT_OK) return st;
     Geometry g;
     geometry(H, W, levels, dtype, 1, 2, g);
-    const int64_t pbytes = (g.partial_floats * (int64_t)sizeof(float) + 255) / 256 * 256;
+    // layout: 256 bytes for the status word, the partials, the level images
+    const int64_t pbytes = 256 + (g.partial_floats * (int64_t)sizeof(float) + 255) / 256 * 256;
     if (pbytes + g.image_bytes > (int64_t)FT_NOALLOC_SCRATCH_BYTES) return FT_ERR_WORKSPACE;
     unsigned char *base = nullptr;
     if ((st = noalloc_scratch(&base)) != FT_OK) return st;
@@ -507,7 +598,8 @@ extern "C" ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dt
     c.max_W = W;
     c.max_levels = levels;
     c.max_pairs = 1;
-    c.partials = reinterpret_cast<float *>(base);
+    c.status = reinterpret_cast<int *>(base);
+    c.partials = reinterpret_cast<float *>(base + 256);
     c.images = base + pbytes;
     c.partial_cap = g.partial_floats;
     c.image_cap = g.image_bytes;
