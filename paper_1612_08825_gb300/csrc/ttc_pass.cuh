@@ -299,6 +299,104 @@ __device__ __forceinline__ void strip_row(const float2 A[5], const float2 B[5], 
     }
 }
 
+// Running state of one thread's strip between rows.
+struct Strip {
+    float2 ps[5];   // previous row: prev + cur per column (biased by 2^23 for integer pixels)
+    float2 pd[5];   // previous row: cur - prev per column
+    float2 phs[4];  // previous row: horizontal differences of ps
+};
+
+// One row step, from the raw pixels of the row: with A = prev frame (unbiased), and
+// the cur frame left biased by 2^23 for integer pixels (sums stay exact below 2^24),
+//   s = A + B, d = B - A per column; hs = s[k+1] - s[k];
+//   Ex = hs(row i) + hs(row i+1), Ey = vd[k] + vd[k+1] with vd = s(i+1) - s(i),
+//   Et = td[k] + td[k+1] with td = d(i) + d(i+1)
+// (the 2x2x2 first differences of Sec. II, times 4).  The neighbour column's s and d
+// come from lane+1 (lane 31 of the right half: its own extra pixel).  Returns the
+// unbiased prev-frame pixels and d of the row's 4 own columns for the pyramid.
+template <typename T, bool MASK>
+__device__ __forceinline__ void row_step(const RawRow<T> &r, int lane, Strip &st, bool first, const float2 xk[4],
+                                         float2 y, bool rowok, int jl, int jr, int jlo, int jhi, float2 acc[NSUM],
+                                         float2 Aout[4], float2 Dout[4])
+{
+    constexpr float BIAS = Pix<T>::INT ? 8388608.f : 0.f;
+    float2 s[5], d[5];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 ab = make_float2(Pix<T>::elem_biased(r.al, k), Pix<T>::elem_biased(r.ar, k));
+        const float2 bb = make_float2(Pix<T>::elem_biased(r.bl, k), Pix<T>::elem_biased(r.br, k));
+        const float2 a = Pix<T>::INT ? unbias2(ab) : ab;
+        s[k] = add2(a, bb);
+        d[k] = sub2(bb, ab);
+        Aout[k] = a;
+        Dout[k] = d[k];
+    }
+    const int src = (lane + 1) & 31;
+    const float s4l = __shfl_sync(0xffffffffu, lane == 0 ? s[0].y : s[0].x, src);
+    const float d4l = __shfl_sync(0xffffffffu, lane == 0 ? d[0].y : d[0].x, src);
+    const float s4r = __shfl_sync(0xffffffffu, s[0].y, src);
+    const float d4r = __shfl_sync(0xffffffffu, d[0].y, src);
+    s[4] = make_float2(s4l, lane == 31 ? (r.a4 + r.b4) + BIAS : s4r);
+    d[4] = make_float2(d4l, lane == 31 ? r.b4 - r.a4 : d4r);
+    float2 hs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) hs[k] = sub2(s[k + 1], s[k]);
+    if (!first) {
+        float2 vd_p, td_p;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float2 vd = sub2(s[k], st.ps[k]);
+            const float2 td = add2(d[k], st.pd[k]);
+            if (k > 0) {
+                float2 ex = add2(hs[k - 1], st.phs[k - 1]);
+                float2 ey = add2(vd_p, vd);
+                float2 et = add2(td_p, td);
+                if (MASK) {
+                    const int cl = jl + k - 1, cr = jr + k - 1;
+                    mask3(ex, ey, et, rowok && cl >= jlo && cl < jhi, rowok && cr >= jlo && cr < jhi);
+                }
+                accum2(acc, ex, ey, et, xk[k - 1], y);
+            }
+            vd_p = vd;
+            td_p = td;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        st.ps[k] = s[k];
+        st.pd[k] = d[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) st.phs[k] = hs[k];
+}
+
+// 2x2 block sums of the next level from two rows' unbiased prev pixels A and
+// differences D (cur = A + D), for the even row (a = true: keep) and the odd row
+// (returns prev-frame sums va0, va1 and cur-frame sums vb0, vb1 of the thread's two
+// level-(l+1) columns, as (left, right) pairs)
+struct Pyr {
+    float2 ha[2], hd[2];
+};
+
+__device__ __forceinline__ void pyr_even(Pyr &py, const float2 A[4], const float2 D[4])
+{
+    py.ha[0] = add2(A[0], A[1]);
+    py.ha[1] = add2(A[2], A[3]);
+    py.hd[0] = add2(D[0], D[1]);
+    py.hd[1] = add2(D[2], D[3]);
+}
+
+__device__ __forceinline__ void pyr_odd(const Pyr &py, const float2 A[4], const float2 D[4], float2 &va0, float2 &va1,
+                                        float2 &vb0, float2 &vb1)
+{
+    va0 = add2(py.ha[0], add2(A[0], A[1]));
+    va1 = add2(py.ha[1], add2(A[2], A[3]));
+    const float2 vd0 = add2(py.hd[0], add2(D[0], D[1]));
+    const float2 vd1 = add2(py.hd[1], add2(D[2], D[3]));
+    vb0 = add2(va0, vd0);
+    vb1 = add2(va1, vd1);
+}
+
 // level-(l+1) pixels (row r1, columns c and c+1) of one frame from the thread's 2x2
 // block sums, written if they exist (r1 < H/2, column < W/2)
 template <typename Tout, bool EDGE>
@@ -345,24 +443,26 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
 #pragma unroll
     for (int r = 0; r < PF; ++r) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r, gcl, raw[r]);
 
-    float2 ps[5], pd[5], ha[2], hb[2];
+    float2 xk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xk[k] = add2(x0, make_float2((float)k, (float)k));
+    float2 y = make_float2((float)(gr0 - 1) + p.yoff, (float)(gr0 - 1) + p.yoff);
+    Strip st;
+    Pyr py;
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
         if (r + PF < 9) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
-        float2 A[5], B[5];
-        unpack5(raw[r], lane, A, B);
+        float2 A[4], D[4];
         const int i = gr0 + r - 1;
-        strip_row<MASK>(A, B, ps, pd, r == 0, x0, (float)i + p.yoff, i >= ilo && i < ihi, gcl, gcl + HALF, jlo,
-                        jhi, acc);
+        row_step<Tin, MASK>(raw[r], lane, st, r == 0, xk, y, i >= ilo && i < ihi, gcl, gcl + HALF, jlo, jhi, acc,
+                            A, D);
+        y = add2(y, make_float2(1.f, 1.f));
         if (WRITE && r < 8) {
             if ((r & 1) == 0) {
-                ha[0] = add2(A[0], A[1]); ha[1] = add2(A[2], A[3]);
-                hb[0] = add2(B[0], B[1]); hb[1] = add2(B[2], B[3]);
+                pyr_even(py, A, D);
             } else {
-                const float2 va0 = add2(ha[0], add2(A[0], A[1]));
-                const float2 va1 = add2(ha[1], add2(A[2], A[3]));
-                const float2 vb0 = add2(hb[0], add2(B[0], B[1]));
-                const float2 vb1 = add2(hb[1], add2(B[2], B[3]));
+                float2 va0, va1, vb0, vb1;
+                pyr_odd(py, A, D, va0, va1, vb0, vb1);
                 const int r1 = (gr0 >> 1) + (r >> 1);
                 const int cl = gcl >> 1, cr = (gcl + HALF) >> 1;
                 store_next<Tout, MASK>(ncur, p.next_pitch, r1, cl, vb0.x, vb1.x, Hn, Wn);

@@ -134,27 +134,29 @@ __device__ __forceinline__ void tile_body(const PassParams &p, const unsigned ch
     unsigned char *nprev = WRITE ? p.next + fprev * p.next_fstride : nullptr;
     unsigned char *ncur = WRITE ? nprev + p.next_fstride : nullptr;
 
-    float2 ps[5], pd[5], ha[2], hb[2];
+    float2 xk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xk[k] = add2(x0, make_float2((float)k, (float)k));
+    float2 y = make_float2((float)(gr0 - 1) + p.yoff, (float)(gr0 - 1) + p.yoff);
+    Strip st;
+    Pyr py;
     RawRow<unsigned char> nxt;
     row_from_smem(buf, 8 * warp, lane, nxt);
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
         const RawRow<unsigned char> cur = nxt;
         if (r < 8) row_from_smem(buf, 8 * warp + r + 1, lane, nxt);
-        float2 A[5], B[5];
-        unpack5(cur, lane, A, B);
+        float2 A[4], D[4];
         const int i = gr0 + r - 1;
-        strip_row<MASK>(A, B, ps, pd, r == 0, x0, (float)i + p.yoff, i >= R0 && i < ihi, gcl, gcl + HALF, C0,
-                        jhi, acc);
+        row_step<unsigned char, MASK>(cur, lane, st, r == 0, xk, y, i >= R0 && i < ihi, gcl, gcl + HALF, C0, jhi,
+                                      acc, A, D);
+        y = add2(y, make_float2(1.f, 1.f));
         if (WRITE && r < 8) {
             if ((r & 1) == 0) {
-                ha[0] = add2(A[0], A[1]); ha[1] = add2(A[2], A[3]);
-                hb[0] = add2(B[0], B[1]); hb[1] = add2(B[2], B[3]);
+                pyr_even(py, A, D);
             } else {
-                const float2 va0 = add2(ha[0], add2(A[0], A[1]));
-                const float2 va1 = add2(ha[1], add2(A[2], A[3]));
-                const float2 vb0 = add2(hb[0], add2(B[0], B[1]));
-                const float2 vb1 = add2(hb[1], add2(B[2], B[3]));
+                float2 va0, va1, vb0, vb1;
+                pyr_odd(py, A, D, va0, va1, vb0, vb1);
                 const int r1 = (gr0 >> 1) + (r >> 1);
                 const int cl = gcl >> 1, cr = (gcl + HALF) >> 1;
                 store_next<unsigned short, MASK>(ncur, p.next_pitch, r1, cl, vb0.x, vb1.x, Hn, Wn);
