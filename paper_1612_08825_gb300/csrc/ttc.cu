@@ -195,6 +195,7 @@ struct Geometry {
     int levels, npairs, nframes;
     int H[FT_MAX_LEVELS], W[FT_MAX_LEVELS];
     int tiles_x[FT_MAX_LEVELS], tiles_y[FT_MAX_LEVELS], ntiles[FT_MAX_LEVELS];
+    int tr[FT_MAX_LEVELS];            // cube rows per tile
     int64_t poff[FT_MAX_LEVELS];      // floats
     int esize[FT_MAX_LEVELS];         // bytes per pixel of the level-l image (l >= 1)
     int64_t pitch[FT_MAX_LEVELS];     // bytes
@@ -203,7 +204,9 @@ struct Geometry {
     int64_t partial_floats, image_bytes;
 };
 
-void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geometry &g)
+// force_tr: 0 picks the tile height per level (16 rows when 64-row tiles would give
+// fewer than ~4 waves of CTAs, so that small levels run as many short CTAs)
+void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geometry &g, int force_tr = 0)
 {
     g.levels = levels;
     g.npairs = npairs;
@@ -212,8 +215,12 @@ void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geom
     for (int l = 0; l < levels; ++l) {
         g.H[l] = H >> l;
         g.W[l] = W >> l;
-        g.tiles_y[l] = (int)ft::ceil_div(g.H[l] - 1, TR);
         g.tiles_x[l] = (int)ft::ceil_div(g.W[l] - 1, TC);
+        int tr = TR;
+        if (force_tr) tr = force_tr;
+        else if ((int64_t)npairs * ft::ceil_div(g.H[l] - 1, TR) * g.tiles_x[l] < 1216) tr = ttc_pass::TR_SMALL;
+        g.tr[l] = tr;
+        g.tiles_y[l] = (int)ft::ceil_div(g.H[l] - 1, tr);
         g.ntiles[l] = g.tiles_y[l] * g.tiles_x[l];
         g.poff[l] = po;
         po += (int64_t)npairs * g.ntiles[l] * NSUM;
@@ -225,10 +232,10 @@ void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geom
         // uint8 frames: exact block sums fit uint16 up to level 4 (255 * 4^4)
         g.esize[l] = (dtype == FT_U8 && l <= 4) ? 2 : 4;
         // padded so that every tile of the pass reads inside the allocation: shifted
-        // edge tiles read up to row H and column W + 2 (tiles_y * TR >= H - 1,
+        // edge tiles read up to row H and column W + 2 (tiles_y * tr >= H - 1,
         // tiles_x * TC >= W - 1)
         g.pitch[l] = (((int64_t)(g.tiles_x[l] * TC + 8) * g.esize[l]) + 15) / 16 * 16;
-        g.fstride[l] = ((g.pitch[l] * (g.tiles_y[l] * TR + 2)) + 255) / 256 * 256;
+        g.fstride[l] = ((g.pitch[l] * (g.tiles_y[l] * g.tr[l] + 2)) + 255) / 256 * 256;
         g.ioff[l] = io;
         io += g.fstride[l] * nframes;
     }
@@ -263,9 +270,12 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     while (lv < max_levels && (max_H >> lv) >= 2 && (max_W >> lv) >= 2) ++lv;
     // the larger of the two layouts: a video of max_pairs + 1 frames or max_pairs
     // independent pairs (two frames each); float frames need the wider images
-    Geometry g;
-    geometry(max_H, max_W, lv, FT_F32, max_pairs, 2 * max_pairs, g);
-    const int64_t pf = g.partial_floats, ib = g.image_bytes;
+    // any tile height a later call may pick
+    Geometry g, g16;
+    geometry(max_H, max_W, lv, FT_F32, max_pairs, 2 * max_pairs, g, TR);
+    geometry(max_H, max_W, lv, FT_F32, max_pairs, 2 * max_pairs, g16, ttc_pass::TR_SMALL);
+    const int64_t pf = std::max(g.partial_floats, g16.partial_floats);
+    const int64_t ib = std::max(g.image_bytes, g16.image_bytes);
     float *part = nullptr;
     unsigned char *img = nullptr;
     // the partials, then 256 bytes holding the status word
@@ -438,6 +448,7 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
         p.W = g.W[l];
         p.tiles_x = g.tiles_x[l];
         p.tiles_y = g.tiles_y[l];
+        p.tr = g.tr[l];
         p.ntiles = g.ntiles[l];
         // cube centre x = j + 1/2 - cx_l, cx_l = (W - 2^l) / 2^(l+1): the level-0 image
         // centre (W-1)/2 expressed in level-l pixel indices
@@ -464,7 +475,7 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
         p.vec = l == 0 ? vec0 : 1;
         p.padded = l == 0 ? 0 : 1;
         bool done = false;
-        if (l == 0 && dtype == FT_U8 && (out_es == 2 || !p.next)) {
+        if (l == 0 && dtype == FT_U8 && g.tr[0] == TR && (out_es == 2 || !p.next)) {
             done = launch_level0_tma(p, prev, cur, pair_stride, npairs, ctx->status, s, &e);
             if (done) ++launches;
         }

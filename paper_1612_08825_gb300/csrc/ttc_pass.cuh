@@ -21,7 +21,8 @@
 
 namespace ttc_pass {
 
-constexpr int TR = 64;          // cube rows per tile
+constexpr int TR = 64;          // cube rows per tile (large levels; small levels use 16)
+constexpr int TR_SMALL = 16;
 constexpr int TC = 256;         // cube columns per tile (two halves of 128)
 constexpr int HALF = TC / 2;
 constexpr int NT = 256;         // threads per CTA
@@ -44,6 +45,7 @@ struct PassParams {
     int64_t pitch;              // bytes between rows of the level-l images
     int H, W;                   // level-l image size
     int tiles_x, tiles_y, ntiles;
+    int tr;                     // cube rows per tile: 64 (8 per warp) or 16 (2 per warp)
     int set;                    // which tiles this launch covers (TileSet)
     int vec;                    // 1: rows allow vector loads
     int padded;                 // 1: images padded past the last tile (context images)
@@ -421,13 +423,13 @@ __device__ __forceinline__ void store_next(unsigned char *img, int64_t pitch, in
 
 // R0, C0: first cube row / column the tile reads; cubes outside [ilo, ihi) x [jlo, jhi)
 // are masked (MASK only)
-template <typename Tin, typename Tout, bool ROWCHK, bool COLCHK, bool MASK, bool WRITE>
+template <typename Tin, typename Tout, bool ROWCHK, bool COLCHK, bool MASK, bool WRITE, int RPW>
 __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, const Tin *fb, int pair, int R0,
                                           int C0, int ilo, int ihi, int jlo, int jhi, float2 acc[NSUM])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gcl = C0 + 4 * lane;
-    const int gr0 = R0 + 8 * warp;
+    const int gr0 = R0 + RPW * warp;
     const float2 x0 = make_float2((float)gcl + p.xoff, (float)(gcl + HALF) + p.xoff);
     const int Hn = p.H >> 1, Wn = p.W >> 1;
     // consecutive pairs of a video share frames (frame t+1 of pair t is frame t+1 of
@@ -438,8 +440,8 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
     unsigned char *nprev = WRITE ? p.next + fprev * p.next_fstride : nullptr;
     unsigned char *ncur = WRITE ? nprev + p.next_fstride : nullptr;
 
-    constexpr int PF = COLCHK ? 1 : FT_TTC_PF;
-    RawRow<Tin> raw[9];
+    constexpr int PF = COLCHK ? 1 : (FT_TTC_PF < RPW ? FT_TTC_PF : RPW);
+    RawRow<Tin> raw[RPW + 1];
 #pragma unroll
     for (int r = 0; r < PF; ++r) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r, gcl, raw[r]);
 
@@ -450,14 +452,14 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
     Strip st;
     Pyr py;
 #pragma unroll
-    for (int r = 0; r < 9; ++r) {
-        if (r + PF < 9) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
+    for (int r = 0; r <= RPW; ++r) {
+        if (r + PF <= RPW) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
         float2 A[4], D[4];
         const int i = gr0 + r - 1;
         row_step<Tin, MASK>(raw[r], lane, st, r == 0, xk, y, i >= ilo && i < ihi, gcl, gcl + HALF, jlo, jhi, acc,
                             A, D);
         y = add2(y, make_float2(1.f, 1.f));
-        if (WRITE && r < 8) {
+        if (WRITE && r < RPW) {
             if ((r & 1) == 0) {
                 pyr_even(py, A, D);
             } else {
@@ -524,7 +526,7 @@ inline int64_t set_size(const PassParams &p)
 
 // ROWCHK / COLCHK: bounds checks on rows / element groups; MASK: cubes outside the
 // tile or the image are masked; SHIFT: edge tiles move inwards (padded images)
-template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK, bool SHIFT>
+template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK, bool SHIFT, int RPW>
 __global__ void __launch_bounds__(NT, FT_TTC_MINB)
 ttc_pass_kernel(const PassParams p)
 {
@@ -532,10 +534,11 @@ ttc_pass_kernel(const PassParams p)
     int pair, ty, tx;
     decode_tile(p, blockIdx.x, pair, ty, tx);
     const int tile = ty * p.tiles_x + tx;
-    const int ilo = ty * TR, jlo = tx * TC;
+    constexpr int TRL = 8 * RPW;            // cube rows of this kernel's tiles
+    const int ilo = ty * TRL, jlo = tx * TC;
     int R0 = ilo, C0 = jlo;
     if (SHIFT) {
-        R0 = min(R0, (p.H - 1 - TR + 1) & ~1);
+        R0 = min(R0, (p.H - 1 - TRL + 1) & ~1);
         C0 = min(C0, (p.W - 1 - TC + 3) & ~3);
     }
     const Tin *fa = reinterpret_cast<const Tin *>(p.prev + (int64_t)pair * p.pair_stride);
@@ -544,41 +547,50 @@ ttc_pass_kernel(const PassParams p)
     float2 acc2[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc2[s] = make_float2(0.f, 0.f);
-    pass_body<Tin, Tout, ROWCHK, COLCHK, MASK, WRITE>(p, fa, fb, pair, R0, C0, ilo, min(ilo + TR, p.H - 1), jlo,
-                                                      min(jlo + TC, p.W - 1), acc2);
+    pass_body<Tin, Tout, ROWCHK, COLCHK, MASK, WRITE, RPW>(p, fa, fb, pair, R0, C0, ilo, min(ilo + TRL, p.H - 1),
+                                                           jlo, min(jlo + TC, p.W - 1), acc2);
     float acc[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc[s] = acc2[s].x + acc2[s].y;
     block_reduce(acc, red, p.partials + ((int64_t)pair * p.ntiles + tile) * NSUM);
 }
 
-template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK, bool SHIFT>
+template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK, bool SHIFT, int RPW>
 int launch_set(PassParams p, int set, int npairs, cudaStream_t s)
 {
     p.set = set;
     const int64_t n = set_size(p) * npairs;
     if (n <= 0) return 0;
-    ttc_pass_kernel<Tin, Tout, WRITE, ROWCHK, COLCHK, MASK, SHIFT><<<(unsigned)n, NT, 0, s>>>(p);
+    ttc_pass_kernel<Tin, Tout, WRITE, ROWCHK, COLCHK, MASK, SHIFT, RPW><<<(unsigned)n, NT, 0, s>>>(p);
     return 1;
 }
 
-// launches the pass; adds the number of kernels launched to *count
+// launches the pass; adds the number of kernels launched to *count.  RPW: cube rows
+// per warp (tiles of 8 * RPW rows)
+template <typename Tin, typename Tout, bool WRITE, int RPW>
+void launch_rpw(const PassParams &p, int npairs, cudaStream_t s, int *count)
+{
+    constexpr int TRL = 8 * RPW;
+    const bool big = p.H >= TRL + 2 && p.W >= TC + 4;
+    int n = 0;
+    if (p.padded && big) {
+        n += launch_set<Tin, Tout, WRITE, false, false, false, false, RPW>(p, SET_INTERIOR, npairs, s);
+        n += launch_set<Tin, Tout, WRITE, false, false, true, true, RPW>(p, SET_EDGES, npairs, s);
+    } else if (p.vec && big) {
+        n += launch_set<Tin, Tout, WRITE, false, false, false, false, RPW>(p, SET_INTERIOR, npairs, s);
+        n += launch_set<Tin, Tout, WRITE, true, false, true, false, RPW>(p, SET_BOTTOM, npairs, s);
+        n += launch_set<Tin, Tout, WRITE, true, true, true, false, RPW>(p, SET_RIGHT, npairs, s);
+    } else {
+        n += launch_set<Tin, Tout, WRITE, true, true, true, false, RPW>(p, SET_ALL, npairs, s);
+    }
+    *count += n;
+}
+
 template <typename Tin, typename Tout, bool WRITE>
 cudaError_t launch_w(const PassParams &p, int npairs, cudaStream_t s, int *count)
 {
-    const bool big = p.H >= TR + 2 && p.W >= TC + 4;
-    int n = 0;
-    if (p.padded && big) {
-        n += launch_set<Tin, Tout, WRITE, false, false, false, false>(p, SET_INTERIOR, npairs, s);
-        n += launch_set<Tin, Tout, WRITE, false, false, true, true>(p, SET_EDGES, npairs, s);
-    } else if (p.vec && big) {
-        n += launch_set<Tin, Tout, WRITE, false, false, false, false>(p, SET_INTERIOR, npairs, s);
-        n += launch_set<Tin, Tout, WRITE, true, false, true, false>(p, SET_BOTTOM, npairs, s);
-        n += launch_set<Tin, Tout, WRITE, true, true, true, false>(p, SET_RIGHT, npairs, s);
-    } else {
-        n += launch_set<Tin, Tout, WRITE, true, true, true, false>(p, SET_ALL, npairs, s);
-    }
-    *count += n;
+    if (p.tr == 64) launch_rpw<Tin, Tout, WRITE, 8>(p, npairs, s, count);
+    else launch_rpw<Tin, Tout, WRITE, 2>(p, npairs, s, count);
     return cudaGetLastError();
 }
 

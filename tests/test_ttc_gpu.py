@@ -206,3 +206,23 @@ def test_full_size_1080p_five_levels():
         for l in range(5):
             check_record(got[t, l], ref[l], 1, l)
     ctx.close()
+
+
+def test_full_size_video_large_tile_paths():
+    """35 consecutive 1080p pairs: levels 0-1 run the 64-row (TMA / vector-load) tile
+    paths, levels 2-4 the 16-row path; sampled pairs against the oracle, and the
+    single-pair entry point (16-row tiles everywhere) within tolerance of the video."""
+    sc = scenes.tilted_plane_scene(H=1080, W=1920, seed=2031)
+    fr = scenes.render_sequence(sc, 36, device=DEV)
+    ctx = ft.TtcContext(1080, 1920, 5, 35)
+    got = ft.results_to_numpy(ctx.solve_sequence(fr, levels=5, mode=1)).reshape(35, 5)
+    assert ctx.last_launch_count >= 5
+    host = fr.cpu().numpy()
+    for t in (0, 17, 34):
+        ref = oracle.ttc_pair(host[t], host[t + 1], levels=5, mode=1)
+        for l in range(5):
+            check_record(got[t, l], ref[l], 1, l)
+        one = ft.results_to_numpy(ctx.solve(fr[t], fr[t + 1], levels=5, mode=1))
+        for l in range(5):
+            check_record(one[l], ref[l], 1, l)
+    ctx.close()
