@@ -206,6 +206,77 @@ def fastconv_sweep(dev, hbm_peak, reps):
     return rows, launches
 
 
+def batch_bench(dev, args):
+    """512 independent pairs of uneven sizes: autotuned work-list launches replayed from
+    a CUDA graph, against the plain per-frame path (one ttc_solve per pair)."""
+    import torch
+    import paper_1612_08825_gb300 as ft
+    import scenes
+    n = args.batch_pairs
+    specs = scenes.uneven_pair_sizes(n, seed=args.seed + 77)
+    pairs = []
+    for i, (h, w, z0, sp) in enumerate(specs):
+        sc = scenes.tilted_plane_scene(H=h, W=w, seed=args.seed + 1000 + i, Z0=z0, speed=sp)
+        fr = scenes.render_sequence(sc, 2, device=dev)
+        pairs.append((fr[0], fr[1]))
+    px = sum(h * w for h, w, _, _ in specs)
+    ctx = ft.TtcContext(1080, 1920, LEVELS, n, device=dev)
+    ctx.batch_prepare(pairs, levels=LEVELS)
+    out = ctx.new_results(n * LEVELS)
+    rows = ctx.batch_autotune(mode=ft.MODE_FOE, reps=2, out=out)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        ctx.batch_run(mode=ft.MODE_FOE, out=out)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctx.batch_run(mode=ft.MODE_FOE, out=out)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.batch_steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_graph = e0.elapsed_time(e1) * 1e-3 / args.batch_steps
+    res = ft.results_to_numpy(out).reshape(n, LEVELS)
+    # the plain per-frame path on the same GPU
+    single = ft.TtcContext(1080, 1920, LEVELS, 1, device=dev)
+    souts = [single.new_results(LEVELS) for _ in range(n)]
+    for i, (a, b) in enumerate(pairs[:8]):
+        single.solve(a, b, levels=LEVELS, mode=ft.MODE_FOE, out=souts[i])
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for i, (a, b) in enumerate(pairs):
+        single.solve(a, b, levels=LEVELS, mode=ft.MODE_FOE, out=souts[i])
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_single = e0.elapsed_time(e1) * 1e-3
+    worst = 0.0
+    checked = 0
+    if not args.no_cpu:
+        import oracle
+        for i in (0, n // 3, n - 1):
+            a, b = pairs[i]
+            ref = oracle.ttc_pair(a.cpu().numpy(), b.cpu().numpy(), levels=LEVELS, mode=1)
+            for l in range(LEVELS):
+                err = np.abs(res[i, l]["sums"] - ref[l]["sums"]) / np.maximum(ref[l]["abssums"], 1e-300)
+                worst = max(worst, float(err.max()))
+            checked += 1
+    ctx.close()
+    single.close()
+    return {"workload": f"{n} independent uint8 pairs, W 160-1920, H 120-1080, {LEVELS} levels, FOE",
+            "megapixels_per_frame_set": px / 1e6, "rows_per_tile_per_level": rows,
+            "graph_pairs_per_s": n / t_graph, "graph_ms_per_batch": t_graph * 1e3,
+            "per_frame_path_pairs_per_s": n / t_single, "per_frame_path_ms": t_single * 1e3,
+            "speedup_vs_per_frame_path": t_single / t_graph,
+            "oracle_pairs_checked": checked, "max_sum_err_rel_abssum": worst}
+
+
 def accuracy(sc, res, levels):
     import paper_1612_08825_gb300 as ft
     import scenes
@@ -359,6 +430,10 @@ def run_ours(args):
         e2e_res = ft.results_to_numpy(hout).reshape(npairs, LEVELS)
         assert e2e_res.tobytes() == res.tobytes(), "host-buffer path disagrees with device path"
 
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = batch_bench(dev, args)
+
     conv_rows = None
     if rank == 0 and not args.no_conv:
         conv_rows, _ = fastconv_sweep(dev, hbm_peak, reps=args.conv_reps)
@@ -392,6 +467,7 @@ def run_ours(args):
             "parity": parity,
             "accuracy": accuracy(sc, res, LEVELS),
             "fastconv": conv_rows,
+            "batch_uneven": batch,
         }
         print(json.dumps(line))
     ctx.close()
@@ -415,6 +491,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-conv", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-pairs", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -209,6 +209,38 @@ ft_status ttc_partial_sums(ttc_ctx *ctx, const void *frames, int64_t frame_strid
 ft_status ttc_reduce_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, void *stream);
 
 /*
+ * Batches of independent frame pairs of different sizes (no counterpart in the paper:
+ * many cameras at once).  ttc_batch_prepare takes the pairs (host array of
+ * descriptors; the frames are device memory owned by the caller and must stay valid
+ * and unchanged in address until the last ttc_batch_run that uses them), checks them,
+ * lays out the context workspace, and uploads a work list of (pair, level, tile)
+ * items and per-(pair, level) descriptors on `stream`.  ttc_batch_run then performs,
+ * for every pair and level, the same computation as ttc_solve (same results up to
+ * rounding; identical for a pair alone or in any batch with the same tile plan) with
+ * two kernel launches per level over the work list plus one merge/solve launch; it
+ * only launches kernels, so a caller may capture it in a CUDA graph and replay it.
+ * out: device, npairs * levels results, out[p * levels + l].
+ * ttc_batch_autotune times, on the prepared batch, 64-row and 16-row tiles for every
+ * level, keeps the faster per level for later prepares on this context, prepares
+ * again with it, and writes the chosen rows per tile to rows_per_tile (host, levels
+ * ints, nullable).  It synchronises `stream`.
+ * Errors: FT_ERR_INVALID_ARG (null, bad dtype/mode, no prepared batch), FT_ERR_SHAPE
+ * (a pair too small for `levels`, pitch), FT_ERR_WORKSPACE (more pairs, levels, or
+ * larger frames than the context was created for), FT_ERR_CUDA.
+ */
+typedef struct {
+    const void *prev;        /* device, H rows of W pixels, row stride pitch_bytes */
+    const void *cur;         /* device, same geometry as prev */
+    int H, W;
+    int64_t pitch_bytes;
+} ttc_pair_desc;
+ft_status ttc_batch_prepare(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npairs, int dtype, int levels,
+                            void *stream);
+ft_status ttc_batch_run(ttc_ctx *ctx, int mode, ttc_level_result *out, void *stream);
+ft_status ttc_batch_autotune(ttc_ctx *ctx, int mode, ttc_level_result *out, int reps, int *rows_per_tile,
+                             void *stream);
+
+/*
  * Timing hook (no counterpart in the paper): when start and end are non-null
  * (cudaEvent_t values passed as void*), every later ttc_partial_sums /
  * ttc_solve_sequence / ttc_solve on this context records `start` on its stream just

@@ -48,6 +48,12 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 _vp = ctypes.c_void_p
 
 
+class PairDesc(ctypes.Structure):
+    """Mirror of ttc_pair_desc."""
+    _fields_ = [("prev", ctypes.c_void_p), ("cur", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("pitch_bytes", ctypes.c_int64)]
+
+
 class FtError(RuntimeError):
     def __init__(self, status: int, what: str):
         name = _lib.ft_status_string(status).decode() if _lib is not None else str(status)
@@ -105,6 +111,12 @@ def load(path: Optional[str] = None):
     L.ttc_ctx_set_level0_events.restype = st
     L.ttc_ctx_last_launch_count.argtypes = [_vp]
     L.ttc_ctx_last_launch_count.restype = ctypes.c_int
+    L.ttc_batch_prepare.argtypes = [_vp, ctypes.POINTER(PairDesc), ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]
+    L.ttc_batch_prepare.restype = st
+    L.ttc_batch_run.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+    L.ttc_batch_run.restype = st
+    L.ttc_batch_autotune.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp]
+    L.ttc_batch_autotune.restype = st
     L.ttc_select_level.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.ttc_select_level.restype = ctypes.c_int
     _lib = L
@@ -338,6 +350,51 @@ class TtcContext:
             host_out.copy_(dev_out, non_blocking=True)
             return host_out
         return dev_out
+
+    def batch_prepare(self, pairs, levels: int = 1):
+        """Prepare a batch of independent pairs [(prev, cur), ...] of any sizes (2-D tensors).
+
+        The tensors must stay alive and in place while the batch is run.
+        """
+        L = load()
+        if len(pairs) == 0:
+            raise ValueError("empty batch")
+        descs = (PairDesc * len(pairs))()
+        dt0 = None
+        for i, (a, b) in enumerate(pairs):
+            _require_cuda(a, "prev")
+            _require_cuda(b, "cur")
+            if a.shape != b.shape or a.dtype != b.dtype or a.dim() != 2:
+                raise ValueError("each pair: 2-D tensors of one shape and dtype")
+            if a.stride(1) != 1 or b.stride(1) != 1 or a.stride(0) != b.stride(0):
+                raise ValueError("rows must be contiguous with one common pitch")
+            dt, es = _frame_args(a)
+            if dt0 is None:
+                dt0 = dt
+            elif dt != dt0:
+                raise ValueError("all pairs of a batch have one dtype")
+            descs[i] = PairDesc(a.data_ptr(), b.data_ptr(), a.shape[0], a.shape[1], a.stride(0) * es)
+        self._batch = (len(pairs), levels, pairs)          # keeps the frames referenced
+        _check(L.ttc_batch_prepare(self._h, descs, len(pairs), dt0, int(levels), _stream_ptr(pairs[0][0])),
+               "ttc_batch_prepare")
+
+    def batch_run(self, mode: int = MODE_FOE, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Run the prepared batch: npairs * levels records, out[p * levels + l] (device)."""
+        L = load()
+        n, levels, _ = self._batch
+        out = self.new_results(n * levels) if out is None else out
+        _check(L.ttc_batch_run(self._h, int(mode), out.data_ptr(), _stream_ptr(out)), "ttc_batch_run")
+        return out
+
+    def batch_autotune(self, mode: int = MODE_FOE, reps: int = 3, out: Optional[torch.Tensor] = None) -> list:
+        """Pick 64- or 16-row tiles per level by timing the prepared batch; returns rows per level."""
+        L = load()
+        n, levels, _ = self._batch
+        out = self.new_results(n * levels) if out is None else out
+        rows = (ctypes.c_int * levels)()
+        _check(L.ttc_batch_autotune(self._h, int(mode), out.data_ptr(), int(reps), rows, _stream_ptr(out)),
+               "ttc_batch_autotune")
+        return [int(rows[i]) for i in range(levels)]
 
     def partial_sums(self, frames: torch.Tensor, levels: int = 1):
         """Stage 1 only (fused pyramid/stencil/products/tile reduction)."""

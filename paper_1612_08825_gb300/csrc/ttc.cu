@@ -111,14 +111,12 @@ __device__ void solve_one(const double s[NSUM], int mode, int level, ttc_level_r
     r->resid = s[9] > 0.0 ? res / s[9] : 0.0;
 }
 
-__global__ void __launch_bounds__(32)
-ttc_solve_kernel(const SolveParams p)
+// One warp: FP64 merge of ntiles FP32 tile partials in a fixed order (lane-strided,
+// then a shuffle tree), scaling to level-l mean-image units, solve; lane 0 writes.
+__device__ __forceinline__ void merge_solve(const float *src, int ntiles, int l, double inv_scale, int64_t ncubes,
+                                            int mode, const int *status, ttc_level_result *out)
 {
-    const int item = blockIdx.x;                 // pair * levels + level
-    const int pair = item / p.levels, l = item - pair * p.levels;
     const int lane = threadIdx.x;
-    const int ntiles = p.ntiles[l];
-    const float *src = p.partials + p.poff[l] + (int64_t)pair * ntiles * NSUM;
     double acc[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc[s] = 0.0;
@@ -131,12 +129,38 @@ ttc_solve_kernel(const SolveParams p)
         for (int s = 0; s < NSUM; ++s) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
     if (lane == 0) {
         ttc_level_result r;
-        for (int s = 0; s < NSUM; ++s) r.sums[s] = acc[s] * p.inv_scale[l];
-        r.n = p.ncubes[l];
-        solve_one(r.sums, p.mode, l, &r);
-        if (*p.status) r.flags |= FT_FLAG_TIMEOUT;
-        p.out[item] = r;
+        for (int s = 0; s < NSUM; ++s) r.sums[s] = acc[s] * inv_scale;
+        r.n = ncubes;
+        solve_one(r.sums, mode, l, &r);
+        if (*status) r.flags |= FT_FLAG_TIMEOUT;
+        *out = r;
     }
+}
+
+__global__ void __launch_bounds__(32)
+ttc_solve_kernel(const SolveParams p)
+{
+    const int item = blockIdx.x;                 // pair * levels + level
+    const int pair = item / p.levels, l = item - pair * p.levels;
+    const int ntiles = p.ntiles[l];
+    merge_solve(p.partials + p.poff[l] + (int64_t)pair * ntiles * NSUM, ntiles, l, p.inv_scale[l], p.ncubes[l],
+                p.mode, p.status, p.out + item);
+}
+
+// partials and cube count of one (pair, level) of a batch
+struct SolveDesc {
+    int64_t poff;                     // floats into the partials
+    int64_t ncubes;
+    int ntiles, level;
+};
+
+__global__ void __launch_bounds__(32)
+ttc_batch_solve_kernel(const float *partials, const SolveDesc *sd, int mode, const int *status,
+                       ttc_level_result *out)
+{
+    const SolveDesc d = sd[blockIdx.x];          // blockIdx.x = pair * levels + level
+    merge_solve(partials + d.poff, d.ntiles, d.level, ldexp(1.0, -4 - 4 * d.level), d.ncubes, mode, status,
+                out + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,6 +281,22 @@ struct ttc_ctx {
     bool ready;
     cudaEvent_t ev0_start, ev0_end;   // optional timing of the level-0 pass
     int launches;                     // kernels launched by the last ttc_partial_sums
+    // batches of pairs of different sizes
+    ttc_pass::PassParams *d_descs;    // [max_levels][max_pairs]
+    int *d_prefix;                    // [max_levels][2][max_pairs + 1]
+    SolveDesc *d_sdesc;               // [max_pairs * max_levels]
+    unsigned char *h_stage;           // pinned staging buffer of the three arrays
+    size_t stage_bytes;
+    cudaEvent_t stage_ev;             // the last upload from h_stage
+    bool stage_pending;
+    struct {
+        int npairs, levels, dtype;
+        int rpw[FT_MAX_LEVELS], in_es[FT_MAX_LEVELS], out_es[FT_MAX_LEVELS];
+        int n_int[FT_MAX_LEVELS], n_edge[FT_MAX_LEVELS];
+        bool ready;
+    } b;
+    int plan_rpw[FT_MAX_LEVELS];      // tile rows per warp per level for batches (0: automatic)
+    ttc_pair_desc *h_pairs;           // host copy of the prepared batch (for the autotuner)
 };
 
 extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max_levels, int max_pairs)
@@ -303,6 +343,31 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->image_cap = ib;
     c->bytes = (size_t)pf * sizeof(float) + 256 + (size_t)ib;
     c->ready = false;
+    // batch descriptors
+    const size_t nd = (size_t)max_levels * max_pairs;
+    const size_t b_desc = nd * sizeof(ttc_pass::PassParams);
+    const size_t b_pre = (size_t)max_levels * 2 * (max_pairs + 1) * sizeof(int);
+    const size_t b_sd = nd * sizeof(SolveDesc);
+    c->stage_bytes = b_desc + b_pre + b_sd;
+    unsigned char *dbuf = nullptr;
+    e = cudaMalloc(&dbuf, c->stage_bytes);
+    if (e == cudaSuccess) e = cudaHostAlloc(&c->h_stage, c->stage_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+    c->h_pairs = new (std::nothrow) ttc_pair_desc[max_pairs];
+    if (e != cudaSuccess || !c->h_pairs) {
+        ft::set_cuda_error(e != cudaSuccess ? e : cudaErrorMemoryAllocation);
+        cudaFree(dbuf);
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        delete[] c->h_pairs;
+        cudaFree(part);
+        cudaFree(img);
+        delete c;
+        return FT_ERR_CUDA;
+    }
+    c->d_descs = reinterpret_cast<ttc_pass::PassParams *>(dbuf);
+    c->d_prefix = reinterpret_cast<int *>(dbuf + b_desc);
+    c->d_sdesc = reinterpret_cast<SolveDesc *>(dbuf + b_desc + b_pre);
+    c->bytes += c->stage_bytes;
     *ctx = c;
     return FT_OK;
 }
@@ -310,8 +375,13 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
 extern "C" void ttc_ctx_destroy(ttc_ctx *ctx)
 {
     if (!ctx) return;
+    if (ctx->stage_pending) cudaEventSynchronize(ctx->stage_ev);
     cudaFree(ctx->partials);
     cudaFree(ctx->images);
+    cudaFree(ctx->d_descs);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+    delete[] ctx->h_pairs;
     delete ctx;
 }
 
@@ -546,6 +616,261 @@ extern "C" ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, 
                                    ft::as_stream(stream));
     if (st != FT_OK) return st;
     return launch_solve(ctx, mode, out, ft::as_stream(stream));
+}
+
+// ---------------------------------------------------------------------------
+// batches of pairs of different sizes
+// ---------------------------------------------------------------------------
+
+namespace {
+
+ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npairs, int dtype, int levels,
+                             cudaStream_t s)
+{
+    if (!ctx || !pairs) return FT_ERR_INVALID_ARG;
+    if (dtype != FT_U8 && dtype != FT_F32) return FT_ERR_INVALID_ARG;
+    if (npairs < 1 || levels < 1) return FT_ERR_INVALID_ARG;
+    if (levels > FT_MAX_LEVELS) return FT_ERR_UNSUPPORTED;
+    if (npairs > ctx->max_pairs || levels > ctx->max_levels) return FT_ERR_WORKSPACE;
+    for (int p = 0; p < npairs; ++p) {
+        const ttc_pair_desc &d = pairs[p];
+        if (!d.prev || !d.cur) return FT_ERR_INVALID_ARG;
+        ft_status st = check_frames(dtype, d.H, d.W, d.pitch_bytes);
+        if (st != FT_OK) return st;
+        if ((st = check_levels(d.H, d.W, levels)) != FT_OK) return st;
+        if (d.H > ctx->max_H || d.W > ctx->max_W) return FT_ERR_WORKSPACE;
+    }
+    // tile rows per warp per level: the plan, or 2 when 64-row tiles give few CTAs
+    int rpw[FT_MAX_LEVELS];
+    for (int l = 0; l < levels; ++l) {
+        if (ctx->plan_rpw[l]) {
+            rpw[l] = ctx->plan_rpw[l];
+            continue;
+        }
+        int64_t t64 = 0;
+        for (int p = 0; p < npairs; ++p)
+            t64 += ft::ceil_div((pairs[p].H >> l) - 1, TR) * ft::ceil_div((pairs[p].W >> l) - 1, TC);
+        rpw[l] = t64 < 1216 ? 2 : 8;
+    }
+    const size_t nd = (size_t)ctx->max_levels * ctx->max_pairs;
+    if (ctx->stage_pending) {
+        cudaError_t e = cudaEventSynchronize(ctx->stage_ev);
+        if (e != cudaSuccess) {
+            ft::set_cuda_error(e);
+            return FT_ERR_CUDA;
+        }
+        ctx->stage_pending = false;
+    }
+    ttc_pass::PassParams *hd = reinterpret_cast<ttc_pass::PassParams *>(ctx->h_stage);
+    int *hpre = reinterpret_cast<int *>(ctx->h_stage + nd * sizeof(ttc_pass::PassParams));
+    SolveDesc *hsd = reinterpret_cast<SolveDesc *>(ctx->h_stage + nd * sizeof(ttc_pass::PassParams) +
+                                                    (size_t)ctx->max_levels * 2 * (ctx->max_pairs + 1) * sizeof(int));
+    const int es0 = dtype == FT_U8 ? 1 : 4;
+    int64_t poff = 0, ioff = 0;
+    int in_es[FT_MAX_LEVELS], out_es[FT_MAX_LEVELS];
+    int64_t n_int[FT_MAX_LEVELS] = {0}, n_edge[FT_MAX_LEVELS] = {0};
+    // per pair: level images (two frames each) and partials, level by level
+    for (int p = 0; p < npairs; ++p) {
+        const ttc_pair_desc &d = pairs[p];
+        int64_t img_off[FT_MAX_LEVELS], img_pitch[FT_MAX_LEVELS], img_fs[FT_MAX_LEVELS];
+        for (int l = 1; l < levels; ++l) {
+            const int es = (dtype == FT_U8 && l <= 4) ? 2 : 4;
+            img_pitch[l] = (((int64_t)(d.W >> l) * es) + 15) / 16 * 16;
+            img_fs[l] = (img_pitch[l] * (d.H >> l) + 255) / 256 * 256;
+            img_off[l] = ioff;
+            ioff += 2 * img_fs[l];
+        }
+        const uintptr_t al = dtype == FT_U8 ? 3 : 15;
+        const int vec0 = ((reinterpret_cast<uintptr_t>(d.prev) & al) == 0 &&
+                          (reinterpret_cast<uintptr_t>(d.cur) & al) == 0 && (d.pitch_bytes & (int64_t)al) == 0)
+                             ? 1 : 0;
+        for (int l = 0; l < levels; ++l) {
+            ttc_pass::PassParams q{};
+            const int H = d.H >> l, W = d.W >> l, tr = 8 * rpw[l];
+            q.H = H;
+            q.W = W;
+            q.tiles_x = (int)ft::ceil_div(W - 1, TC);
+            q.tiles_y = (int)ft::ceil_div(H - 1, tr);
+            q.ntiles = q.tiles_x * q.tiles_y;
+            q.tr = tr;
+            if (l == 0) {
+                q.prev = static_cast<const unsigned char *>(d.prev);
+                q.cur = static_cast<const unsigned char *>(d.cur);
+                q.pitch = d.pitch_bytes;
+                q.vec = vec0;
+            } else {
+                q.prev = ctx->images + img_off[l];
+                q.cur = q.prev + img_fs[l];
+                q.pitch = img_pitch[l];
+                q.vec = 1;
+            }
+            q.set = q.vec ? ttc_pass::SET_EDGES : ttc_pass::SET_ALL;
+            const double pl = (double)(1 << l);
+            q.xoff = (float)(0.5 - ((double)d.W - pl) / (2.0 * pl));
+            q.yoff = (float)(0.5 - ((double)d.H - pl) / (2.0 * pl));
+            q.partials = ctx->partials + poff;
+            if (l + 1 < levels) {
+                q.next = ctx->images + img_off[l + 1];
+                q.next_fstride = img_fs[l + 1];
+                q.next_pitch = img_pitch[l + 1];
+            }
+            q.write_prev = 1;
+            hd[(size_t)l * ctx->max_pairs + p] = q;
+            const int ni = q.vec ? (q.tiles_y - 1) * (q.tiles_x - 1) : 0;
+            const int ne = q.vec ? q.tiles_x + q.tiles_y - 1 : q.ntiles;
+            int *pi = hpre + ((size_t)l * 2 + 0) * (ctx->max_pairs + 1);
+            int *pe = hpre + ((size_t)l * 2 + 1) * (ctx->max_pairs + 1);
+            pi[p] = (int)n_int[l];
+            pe[p] = (int)n_edge[l];
+            n_int[l] += ni;
+            n_edge[l] += ne;
+            pi[p + 1] = (int)n_int[l];
+            pe[p + 1] = (int)n_edge[l];
+            SolveDesc sd;
+            sd.poff = poff;
+            sd.ncubes = (int64_t)(H - 1) * (W - 1);
+            sd.ntiles = q.ntiles;
+            sd.level = l;
+            hsd[(size_t)p * levels + l] = sd;
+            poff += (int64_t)q.ntiles * NSUM;
+            in_es[l] = l == 0 ? es0 : ((dtype == FT_U8 && l <= 4) ? 2 : 4);
+            out_es[l] = (dtype == FT_U8 && l + 1 <= 4) ? 2 : 4;
+        }
+    }
+    if (poff > ctx->partial_cap || ioff > ctx->image_cap) return FT_ERR_WORKSPACE;
+    for (int l = 0; l < levels; ++l)
+        if (n_int[l] > 0x7fffffffLL || n_edge[l] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
+    cudaError_t e = cudaMemcpyAsync(ctx->d_descs, ctx->h_stage, ctx->stage_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev, s);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    ctx->stage_pending = true;
+    if (pairs != ctx->h_pairs)
+        for (int p = 0; p < npairs; ++p) ctx->h_pairs[p] = pairs[p];
+    ctx->b.npairs = npairs;
+    ctx->b.levels = levels;
+    ctx->b.dtype = dtype;
+    for (int l = 0; l < levels; ++l) {
+        ctx->b.rpw[l] = rpw[l];
+        ctx->b.in_es[l] = in_es[l];
+        ctx->b.out_es[l] = out_es[l];
+        ctx->b.n_int[l] = (int)n_int[l];
+        ctx->b.n_edge[l] = (int)n_edge[l];
+    }
+    ctx->b.ready = true;
+    return FT_OK;
+}
+
+template <typename Tin>
+cudaError_t batch_level(ttc_ctx *ctx, int l, int *count, cudaStream_t s)
+{
+    const auto &b = ctx->b;
+    const ttc_pass::PassParams *descs = ctx->d_descs + (size_t)l * ctx->max_pairs;
+    const int *pi = ctx->d_prefix + ((size_t)l * 2 + 0) * (ctx->max_pairs + 1);
+    const int *pe = ctx->d_prefix + ((size_t)l * 2 + 1) * (ctx->max_pairs + 1);
+    const bool write = l + 1 < b.levels;
+    if (b.out_es[l] == 2)
+        return ttc_pass::launch_batch<Tin, unsigned short>(descs, pi, pe, b.n_int[l], b.n_edge[l], b.npairs, write,
+                                                           b.rpw[l], s, count);
+    return ttc_pass::launch_batch<Tin, float>(descs, pi, pe, b.n_int[l], b.n_edge[l], b.npairs, write, b.rpw[l], s,
+                                              count);
+}
+
+// launches of one prepared batch; level_ev (nullable): levels + 1 events around the levels
+ft_status batch_run_impl(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream_t s, cudaEvent_t *level_ev)
+{
+    if (!ctx || !out) return FT_ERR_INVALID_ARG;
+    if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
+    if (!ctx->b.ready) return FT_ERR_INVALID_ARG;
+    const auto &b = ctx->b;
+    int count = 0;
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
+    for (int l = 0; l < b.levels && e == cudaSuccess; ++l) {
+        if (level_ev) e = cudaEventRecord(level_ev[l], s);
+        if (e != cudaSuccess) break;
+        if (b.in_es[l] == 1) e = batch_level<unsigned char>(ctx, l, &count, s);
+        else if (b.in_es[l] == 2) e = batch_level<unsigned short>(ctx, l, &count, s);
+        else e = batch_level<float>(ctx, l, &count, s);
+    }
+    if (e == cudaSuccess && level_ev) e = cudaEventRecord(level_ev[b.levels], s);
+    if (e == cudaSuccess) {
+        ttc_batch_solve_kernel<<<(unsigned)(b.npairs * b.levels), 32, 0, s>>>(ctx->partials, ctx->d_sdesc, mode,
+                                                                              ctx->status, out);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    ctx->launches = count + 1;
+    return FT_OK;
+}
+
+}  // namespace
+
+extern "C" ft_status ttc_batch_prepare(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npairs, int dtype, int levels,
+                                       void *stream)
+{
+    return batch_prepare_impl(ctx, pairs, npairs, dtype, levels, ft::as_stream(stream));
+}
+
+extern "C" ft_status ttc_batch_run(ttc_ctx *ctx, int mode, ttc_level_result *out, void *stream)
+{
+    return batch_run_impl(ctx, mode, out, ft::as_stream(stream), nullptr);
+}
+
+extern "C" ft_status ttc_batch_autotune(ttc_ctx *ctx, int mode, ttc_level_result *out, int reps, int *rows_per_tile,
+                                        void *stream)
+{
+    if (!ctx || !out || reps < 1) return FT_ERR_INVALID_ARG;
+    if (!ctx->b.ready) return FT_ERR_INVALID_ARG;
+    cudaStream_t s = ft::as_stream(stream);
+    const int npairs = ctx->b.npairs, levels = ctx->b.levels, dtype = ctx->b.dtype;
+    cudaEvent_t ev[FT_MAX_LEVELS + 1];
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made <= levels && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    float best_ms[FT_MAX_LEVELS];
+    int best[FT_MAX_LEVELS];
+    ft_status st = FT_OK;
+    const int cand[2] = {8, 2};
+    for (int c = 0; c < 2 && st == FT_OK && e == cudaSuccess; ++c) {
+        for (int l = 0; l < levels; ++l) ctx->plan_rpw[l] = cand[c];
+        st = batch_prepare_impl(ctx, ctx->h_pairs, npairs, dtype, levels, s);
+        float ms[FT_MAX_LEVELS] = {0};
+        for (int r = 0; r <= reps && st == FT_OK; ++r) {       // the first run warms up
+            st = batch_run_impl(ctx, mode, out, s, ev);
+            if (st != FT_OK) break;
+            e = cudaEventSynchronize(ev[levels]);
+            if (e != cudaSuccess) break;
+            for (int l = 0; l < levels && r > 0; ++l) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, ev[l], ev[l + 1]);
+                ms[l] += t;
+            }
+        }
+        for (int l = 0; l < levels; ++l)
+            if (c == 0 || ms[l] < best_ms[l]) {
+                best_ms[l] = ms[l];
+                best[l] = cand[c];
+            }
+    }
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        st = FT_ERR_CUDA;
+    }
+    if (st != FT_OK) {
+        for (int l = 0; l < FT_MAX_LEVELS; ++l) ctx->plan_rpw[l] = 0;
+        return st;
+    }
+    for (int l = 0; l < levels; ++l) {
+        ctx->plan_rpw[l] = best[l];
+        if (rows_per_tile) rows_per_tile[l] = 8 * best[l];
+    }
+    return batch_prepare_impl(ctx, ctx->h_pairs, npairs, dtype, levels, s);
 }
 
 // ---------------------------------------------------------------------------

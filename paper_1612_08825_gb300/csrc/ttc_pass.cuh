@@ -600,4 +600,85 @@ cudaError_t launch(const PassParams &p, int npairs, cudaStream_t s, int *count)
     return p.next ? launch_w<Tin, Tout, true>(p, npairs, s, count) : launch_w<Tin, Tout, false>(p, npairs, s, count);
 }
 
+// ---------------------------------------------------------------------------
+// batches of frame pairs of different sizes: one launch per level and tile class
+// over a work list of (pair, tile) items
+// ---------------------------------------------------------------------------
+
+// descs: pass parameters of every pair at this level (pair-local: prev/cur, partials
+// and next-level images of that pair only); prefix: npairs + 1 running item counts
+// of this tile class.  CHECK = false: interior tiles (vector loads, no masks);
+// CHECK = true: edge tiles (element checks, masks).
+template <typename Tin, typename Tout, bool WRITE, bool CHECK, int RPW>
+__global__ void __launch_bounds__(NT, FT_TTC_MINB)
+ttc_batch_kernel(const PassParams *__restrict__ descs, const int *__restrict__ prefix, int npairs)
+{
+    __shared__ float red[NSUM * NT];
+    constexpr int TRL = 8 * RPW;
+    const int item = blockIdx.x;
+    int lo = 0, hi = npairs - 1;                 // last pair whose first item <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    const PassParams &p = descs[lo];
+    const int local = item - __ldg(prefix + lo);
+    int ty, tx;
+    if (!CHECK) {
+        ty = local / (p.tiles_x - 1);
+        tx = local - ty * (p.tiles_x - 1);
+    } else if (p.set == SET_ALL) {
+        ty = local / p.tiles_x;
+        tx = local - ty * p.tiles_x;
+    } else if (local < p.tiles_x) {
+        ty = p.tiles_y - 1;
+        tx = local;
+    } else {
+        ty = local - p.tiles_x;
+        tx = p.tiles_x - 1;
+    }
+    const int tile = ty * p.tiles_x + tx;
+    const int R0 = ty * TRL, C0 = tx * TC;
+    const Tin *fa = reinterpret_cast<const Tin *>(p.prev);
+    const Tin *fb = reinterpret_cast<const Tin *>(p.cur);
+    float2 acc2[NSUM];
+#pragma unroll
+    for (int s = 0; s < NSUM; ++s) acc2[s] = make_float2(0.f, 0.f);
+    pass_body<Tin, Tout, CHECK, CHECK, CHECK, WRITE, RPW>(p, fa, fb, 0, R0, C0, R0, min(R0 + TRL, p.H - 1), C0,
+                                                          min(C0 + TC, p.W - 1), acc2);
+    float acc[NSUM];
+#pragma unroll
+    for (int s = 0; s < NSUM; ++s) acc[s] = acc2[s].x + acc2[s].y;
+    block_reduce(acc, red, p.partials + (int64_t)tile * NSUM);
+}
+
+template <typename Tin, typename Tout, bool WRITE, int RPW>
+void launch_batch_rpw(const PassParams *descs, const int *pre_int, const int *pre_edge, int n_int, int n_edge,
+                      int npairs, cudaStream_t s, int *count)
+{
+    if (n_int > 0) {
+        ttc_batch_kernel<Tin, Tout, WRITE, false, RPW><<<n_int, NT, 0, s>>>(descs, pre_int, npairs);
+        ++*count;
+    }
+    if (n_edge > 0) {
+        ttc_batch_kernel<Tin, Tout, WRITE, true, RPW><<<n_edge, NT, 0, s>>>(descs, pre_edge, npairs);
+        ++*count;
+    }
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_batch(const PassParams *descs, const int *pre_int, const int *pre_edge, int n_int, int n_edge,
+                         int npairs, bool write, int rpw, cudaStream_t s, int *count)
+{
+    if (write) {
+        if (rpw == 8) launch_batch_rpw<Tin, Tout, true, 8>(descs, pre_int, pre_edge, n_int, n_edge, npairs, s, count);
+        else launch_batch_rpw<Tin, Tout, true, 2>(descs, pre_int, pre_edge, n_int, n_edge, npairs, s, count);
+    } else {
+        if (rpw == 8) launch_batch_rpw<Tin, Tout, false, 8>(descs, pre_int, pre_edge, n_int, n_edge, npairs, s, count);
+        else launch_batch_rpw<Tin, Tout, false, 2>(descs, pre_int, pre_edge, n_int, n_edge, npairs, s, count);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace ttc_pass
