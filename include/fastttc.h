@@ -233,12 +233,46 @@ typedef struct {
     const void *cur;         /* device, same geometry as prev */
     int H, W;
     int64_t pitch_bytes;
+    /* Per-frame pyramids owned by the caller (both nullable; see ttc_pyramid_layout).
+     * prev_pyramid: levels 1 .. levels-1 of `prev`, as an earlier ttc_batch_run wrote
+     * them into a cur_pyramid of the same H, W, dtype and levels; read only.
+     * cur_pyramid: receives levels 1 .. levels-1 of `cur`.  A null pointer puts that
+     * frame's pyramid in the context workspace instead.  The two must differ, and no
+     * block may be one pair's cur_pyramid and another pair's prev_pyramid in the same
+     * batch (the results of such a batch are unspecified).  16-byte aligned. */
+    const void *prev_pyramid;
+    void *cur_pyramid;
 } ttc_pair_desc;
 ft_status ttc_batch_prepare(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npairs, int dtype, int levels,
                             void *stream);
 ft_status ttc_batch_run(ttc_ctx *ctx, int mode, ttc_level_result *out, void *stream);
 ft_status ttc_batch_autotune(ttc_ctx *ctx, int mode, ttc_level_result *out, int reps, int *rows_per_tile,
                              void *stream);
+
+/*
+ * Layout of one frame's pyramid block (levels 1 .. levels-1 of the 2x2 block-sum
+ * pyramid of Sec. V-B, no counterpart as a buffer in the paper): level l is an image of
+ * floor(H/2^l) rows of floor(W/2^l) pixels, uint16 exact sums of 4^l pixels for uint8
+ * frames up to level 4 and float beyond (float means for float frames), starting at
+ * byte offsets[l] of the block with row stride pitches[l].  offsets and pitches: host,
+ * levels entries each (entry 0 is set to 0), nullable; *bytes: the block size (0 when
+ * levels == 1).  A serving loop keeps two blocks per stream and swaps them each frame,
+ * so that each frame's pyramid is built once.
+ * Errors: FT_ERR_INVALID_ARG (null bytes, bad dtype), FT_ERR_SHAPE (frame too small
+ * for `levels`), FT_ERR_UNSUPPORTED (levels > FT_MAX_LEVELS).
+ */
+ft_status ttc_pyramid_layout(int H, int W, int levels, int dtype, int64_t *offsets, int64_t *pitches,
+                             int64_t *bytes);
+
+/*
+ * Fixes the tile height of every level for later ttc_batch_prepare calls on this
+ * context (no counterpart in the paper).  rows_per_tile: host, levels entries, each 16
+ * or 64; null clears the plan (automatic choice per batch).  With a fixed plan, the
+ * results of a pair do not depend on the other pairs of its batch.
+ * Errors: FT_ERR_INVALID_ARG (null context, bad entry, levels < 1),
+ * FT_ERR_UNSUPPORTED (levels > FT_MAX_LEVELS).
+ */
+ft_status ttc_batch_set_plan(ttc_ctx *ctx, const int *rows_per_tile, int levels);
 
 /*
  * Timing hook (no counterpart in the paper): when start and end are non-null

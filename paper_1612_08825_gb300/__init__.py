@@ -28,7 +28,7 @@ __all__ = [
 
 MODE_TTC, MODE_FOE = 0, 1
 DTYPE_U8, DTYPE_F32 = 0, 1
-FLAG_SINGULAR, FLAG_C_ZERO, FLAG_RECEDING = 1, 2, 4
+FLAG_SINGULAR, FLAG_C_ZERO, FLAG_RECEDING, FLAG_TIMEOUT = 1, 2, 4, 8
 MAX_LEVELS = 7
 MAX_NDIM = 8
 
@@ -51,7 +51,7 @@ _vp = ctypes.c_void_p
 class PairDesc(ctypes.Structure):
     """Mirror of ttc_pair_desc."""
     _fields_ = [("prev", ctypes.c_void_p), ("cur", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
-                ("pitch_bytes", ctypes.c_int64)]
+                ("pitch_bytes", ctypes.c_int64), ("prev_pyramid", ctypes.c_void_p), ("cur_pyramid", ctypes.c_void_p)]
 
 
 class FtError(RuntimeError):
@@ -117,6 +117,10 @@ def load(path: Optional[str] = None):
     L.ttc_batch_run.restype = st
     L.ttc_batch_autotune.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp]
     L.ttc_batch_autotune.restype = st
+    L.ttc_pyramid_layout.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _i64p, _i64p]
+    L.ttc_pyramid_layout.restype = st
+    L.ttc_batch_set_plan.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.ttc_batch_set_plan.restype = st
     L.ttc_select_level.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.ttc_select_level.restype = ctypes.c_int
     _lib = L
@@ -218,6 +222,21 @@ def results_to_numpy(t: torch.Tensor) -> np.ndarray:
     """Device/host byte tensor of ttc_level_result records -> numpy structured array."""
     a = t.detach().to("cpu").contiguous().numpy()
     return a.view(RESULT_DTYPE).reshape(-1)
+
+
+def pyramid_layout(H: int, W: int, levels: int, dtype=torch.uint8) -> dict:
+    """Layout of one frame's pyramid block (levels 1 .. levels-1): offsets, pitches, bytes."""
+    L = load()
+    dt = DTYPE_U8 if dtype == torch.uint8 else DTYPE_F32 if dtype == torch.float32 else None
+    if dt is None:
+        raise ValueError("frames are uint8 or float32")
+    n = max(int(levels), 1)
+    off = (ctypes.c_int64 * n)()
+    pit = (ctypes.c_int64 * n)()
+    nbytes = ctypes.c_int64(0)
+    _check(L.ttc_pyramid_layout(int(H), int(W), int(levels), dt, off, pit, ctypes.byref(nbytes)),
+           "ttc_pyramid_layout")
+    return {"offsets": list(off), "pitches": list(pit), "bytes": int(nbytes.value)}
 
 
 def select_level(results: np.ndarray, rule: int = 0) -> int:
@@ -352,16 +371,24 @@ class TtcContext:
         return dev_out
 
     def batch_prepare(self, pairs, levels: int = 1):
-        """Prepare a batch of independent pairs [(prev, cur), ...] of any sizes (2-D tensors).
+        """Prepare a batch of independent pairs of any sizes.
 
-        The tensors must stay alive and in place while the batch is run.
+        Each entry is (prev, cur) or (prev, cur, prev_pyramid, cur_pyramid): 2-D frame
+        tensors, and optional uint8 device blocks of ``pyramid_layout(...)['bytes']``
+        bytes (None: that frame's pyramid stays in the context workspace).  The tensors
+        must stay alive and in place while the batch is run.
         """
         L = load()
         if len(pairs) == 0:
             raise ValueError("empty batch")
         descs = (PairDesc * len(pairs))()
         dt0 = None
-        for i, (a, b) in enumerate(pairs):
+        for i, entry in enumerate(pairs):
+            a, b = entry[0], entry[1]
+            pa, pb = (entry[2], entry[3]) if len(entry) > 2 else (None, None)
+            for blk, what in ((pa, "prev_pyramid"), (pb, "cur_pyramid")):
+                if blk is not None:
+                    _require_cuda(blk, what)
             _require_cuda(a, "prev")
             _require_cuda(b, "cur")
             if a.shape != b.shape or a.dtype != b.dtype or a.dim() != 2:
@@ -373,7 +400,8 @@ class TtcContext:
                 dt0 = dt
             elif dt != dt0:
                 raise ValueError("all pairs of a batch have one dtype")
-            descs[i] = PairDesc(a.data_ptr(), b.data_ptr(), a.shape[0], a.shape[1], a.stride(0) * es)
+            descs[i] = PairDesc(a.data_ptr(), b.data_ptr(), a.shape[0], a.shape[1], a.stride(0) * es,
+                                pa.data_ptr() if pa is not None else None, pb.data_ptr() if pb is not None else None)
         self._batch = (len(pairs), levels, pairs)          # keeps the frames referenced
         _check(L.ttc_batch_prepare(self._h, descs, len(pairs), dt0, int(levels), _stream_ptr(pairs[0][0])),
                "ttc_batch_prepare")
@@ -395,6 +423,15 @@ class TtcContext:
         _check(L.ttc_batch_autotune(self._h, int(mode), out.data_ptr(), int(reps), rows, _stream_ptr(out)),
                "ttc_batch_autotune")
         return [int(rows[i]) for i in range(levels)]
+
+    def batch_set_plan(self, rows_per_tile=None, levels: Optional[int] = None):
+        """Fix the tile height (16 or 64 rows) per level for later prepares; None: automatic."""
+        L = load()
+        if rows_per_tile is None:
+            _check(L.ttc_batch_set_plan(self._h, None, int(levels or 1)), "ttc_batch_set_plan")
+            return
+        arr = (ctypes.c_int * len(rows_per_tile))(*[int(r) for r in rows_per_tile])
+        _check(L.ttc_batch_set_plan(self._h, arr, len(rows_per_tile)), "ttc_batch_set_plan")
 
     def partial_sums(self, frames: torch.Tensor, levels: int = 1):
         """Stage 1 only (fused pyramid/stencil/products/tile reduction)."""

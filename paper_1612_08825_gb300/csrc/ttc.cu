@@ -213,6 +213,15 @@ ft_status check_levels(int H, int W, int levels)
     return FT_OK;
 }
 
+// level-l image (l >= 1) of one frame in a batch: row pitch and bytes, the same in
+// the context workspace and in caller-owned pyramid blocks
+void batch_level_image(int H, int W, int l, int dtype, int64_t *pitch, int64_t *bytes)
+{
+    const int es = (dtype == FT_U8 && l <= 4) ? 2 : 4;
+    *pitch = ((int64_t)(W >> l) * es + 15) / 16 * 16;
+    *bytes = (*pitch * (H >> l) + 255) / 256 * 256;
+}
+
 // Per-level geometry of one request: tiles, partial-sum offsets, and the layout of
 // the level images kept in the context (level l >= 1 of every frame).
 struct Geometry {
@@ -635,6 +644,9 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
     for (int p = 0; p < npairs; ++p) {
         const ttc_pair_desc &d = pairs[p];
         if (!d.prev || !d.cur) return FT_ERR_INVALID_ARG;
+        if ((reinterpret_cast<uintptr_t>(d.prev_pyramid) & 15) || (reinterpret_cast<uintptr_t>(d.cur_pyramid) & 15))
+            return FT_ERR_INVALID_ARG;
+        if (d.prev_pyramid && d.prev_pyramid == d.cur_pyramid) return FT_ERR_INVALID_ARG;
         ft_status st = check_frames(dtype, d.H, d.W, d.pitch_bytes);
         if (st != FT_OK) return st;
         if ((st = check_levels(d.H, d.W, levels)) != FT_OK) return st;
@@ -669,17 +681,31 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
     int64_t poff = 0, ioff = 0;
     int in_es[FT_MAX_LEVELS], out_es[FT_MAX_LEVELS];
     int64_t n_int[FT_MAX_LEVELS] = {0}, n_edge[FT_MAX_LEVELS] = {0};
-    // per pair: level images (two frames each) and partials, level by level
+    // per pair: level images and partials, level by level.  A frame's level images
+    // live in the caller's pyramid block when the descriptor gives one, else in the
+    // context workspace (images + ioff).
     for (int p = 0; p < npairs; ++p) {
         const ttc_pair_desc &d = pairs[p];
-        int64_t img_off[FT_MAX_LEVELS], img_pitch[FT_MAX_LEVELS], img_fs[FT_MAX_LEVELS];
+        int64_t img_pitch[FT_MAX_LEVELS], img_fs[FT_MAX_LEVELS];
+        int64_t prev_off[FT_MAX_LEVELS], cur_off[FT_MAX_LEVELS];   // workspace offsets, -1: caller block
+        int64_t pyr_off[FT_MAX_LEVELS];                             // offsets in a pyramid block
+        int64_t po = 0;
         for (int l = 1; l < levels; ++l) {
-            const int es = (dtype == FT_U8 && l <= 4) ? 2 : 4;
-            img_pitch[l] = (((int64_t)(d.W >> l) * es) + 15) / 16 * 16;
-            img_fs[l] = (img_pitch[l] * (d.H >> l) + 255) / 256 * 256;
-            img_off[l] = ioff;
-            ioff += 2 * img_fs[l];
+            batch_level_image(d.H, d.W, l, dtype, &img_pitch[l], &img_fs[l]);
+            pyr_off[l] = po;
+            po += img_fs[l];
+            prev_off[l] = d.prev_pyramid ? -1 : ioff;
+            if (!d.prev_pyramid) ioff += img_fs[l];
+            cur_off[l] = d.cur_pyramid ? -1 : ioff;
+            if (!d.cur_pyramid) ioff += img_fs[l];
         }
+        auto prev_img = [&](int l) -> unsigned char * {
+            return prev_off[l] >= 0 ? ctx->images + prev_off[l] : nullptr;
+        };
+        auto cur_img = [&](int l) -> unsigned char * {
+            return cur_off[l] >= 0 ? ctx->images + cur_off[l]
+                                   : static_cast<unsigned char *>(d.cur_pyramid) + pyr_off[l];
+        };
         const uintptr_t al = dtype == FT_U8 ? 3 : 15;
         const int vec0 = ((reinterpret_cast<uintptr_t>(d.prev) & al) == 0 &&
                           (reinterpret_cast<uintptr_t>(d.cur) & al) == 0 && (d.pitch_bytes & (int64_t)al) == 0)
@@ -699,8 +725,9 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
                 q.pitch = d.pitch_bytes;
                 q.vec = vec0;
             } else {
-                q.prev = ctx->images + img_off[l];
-                q.cur = q.prev + img_fs[l];
+                q.prev = prev_off[l] >= 0 ? ctx->images + prev_off[l]
+                                          : static_cast<const unsigned char *>(d.prev_pyramid) + pyr_off[l];
+                q.cur = cur_img(l);
                 q.pitch = img_pitch[l];
                 q.vec = 1;
             }
@@ -709,12 +736,12 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
             q.xoff = (float)(0.5 - ((double)d.W - pl) / (2.0 * pl));
             q.yoff = (float)(0.5 - ((double)d.H - pl) / (2.0 * pl));
             q.partials = ctx->partials + poff;
+            q.write_prev = d.prev_pyramid ? -1 : 1;
             if (l + 1 < levels) {
-                q.next = ctx->images + img_off[l + 1];
-                q.next_fstride = img_fs[l + 1];
+                q.next = prev_img(l + 1);
+                q.next_cur = cur_img(l + 1);
                 q.next_pitch = img_pitch[l + 1];
             }
-            q.write_prev = 1;
             hd[(size_t)l * ctx->max_pairs + p] = q;
             const int ni = q.vec ? (q.tiles_y - 1) * (q.tiles_x - 1) : 0;
             const int ne = q.vec ? q.tiles_x + q.tiles_y - 1 : q.ntiles;
@@ -871,6 +898,41 @@ extern "C" ft_status ttc_batch_autotune(ttc_ctx *ctx, int mode, ttc_level_result
         if (rows_per_tile) rows_per_tile[l] = 8 * best[l];
     }
     return batch_prepare_impl(ctx, ctx->h_pairs, npairs, dtype, levels, s);
+}
+
+extern "C" ft_status ttc_pyramid_layout(int H, int W, int levels, int dtype, int64_t *offsets, int64_t *pitches,
+                                        int64_t *bytes)
+{
+    if (!bytes || (dtype != FT_U8 && dtype != FT_F32)) return FT_ERR_INVALID_ARG;
+    if (H < 2 || W < 2) return FT_ERR_SHAPE;
+    const ft_status st = check_levels(H, W, levels);
+    if (st != FT_OK) return st;
+    int64_t po = 0;
+    if (offsets) offsets[0] = 0;
+    if (pitches) pitches[0] = 0;
+    for (int l = 1; l < levels; ++l) {
+        int64_t pitch, fs;
+        batch_level_image(H, W, l, dtype, &pitch, &fs);
+        if (offsets) offsets[l] = po;
+        if (pitches) pitches[l] = pitch;
+        po += fs;
+    }
+    *bytes = po;
+    return FT_OK;
+}
+
+extern "C" ft_status ttc_batch_set_plan(ttc_ctx *ctx, const int *rows_per_tile, int levels)
+{
+    if (!ctx || levels < 1) return FT_ERR_INVALID_ARG;
+    if (levels > FT_MAX_LEVELS) return FT_ERR_UNSUPPORTED;
+    if (!rows_per_tile) {
+        for (int l = 0; l < FT_MAX_LEVELS; ++l) ctx->plan_rpw[l] = 0;
+        return FT_OK;
+    }
+    for (int l = 0; l < levels; ++l)
+        if (rows_per_tile[l] != 8 * 8 && rows_per_tile[l] != 8 * 2) return FT_ERR_INVALID_ARG;
+    for (int l = 0; l < FT_MAX_LEVELS; ++l) ctx->plan_rpw[l] = l < levels ? rows_per_tile[l] / 8 : 0;
+    return FT_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -54,7 +54,10 @@ struct PassParams {
     unsigned char *next;        // level-(l+1) image of frame 0, or null
     int64_t next_fstride;       // bytes between frames of `next`
     int64_t next_pitch;         // bytes between rows of `next`
-    int write_prev;             // 0: video (frame t+1 of pair t is shared); 1: independent pairs
+    int write_prev;             // 0: video (frame t+1 of pair t is shared); 1: independent pairs;
+                                // -1: the first frame's level l+1 exists already (not written)
+    unsigned char *next_cur;    // non-null: level-(l+1) image of the second frame (one pair per launch
+                                // item); null: the frame after the first one in `next`
 };
 
 // ---------------------------------------------------------------------------
@@ -435,10 +438,10 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
     // consecutive pairs of a video share frames (frame t+1 of pair t is frame t+1 of
     // the next pair): the first frame is written by pair 0 only; independent pairs
     // own two frames each
-    const bool wprev = WRITE && (p.write_prev || pair == 0);
-    const int64_t fprev = p.write_prev ? 2 * (int64_t)pair : (int64_t)pair;
-    unsigned char *nprev = WRITE ? p.next + fprev * p.next_fstride : nullptr;
-    unsigned char *ncur = WRITE ? nprev + p.next_fstride : nullptr;
+    const bool wprev = WRITE && (p.write_prev == 1 || (p.write_prev == 0 && pair == 0));
+    const int64_t fprev = p.write_prev == 1 ? 2 * (int64_t)pair : (int64_t)pair;
+    unsigned char *nprev = WRITE && wprev ? p.next + fprev * p.next_fstride : nullptr;
+    unsigned char *ncur = WRITE ? (p.next_cur ? p.next_cur : p.next + (fprev + 1) * p.next_fstride) : nullptr;
 
     constexpr int PF = COLCHK ? 1 : (FT_TTC_PF < RPW ? FT_TTC_PF : RPW);
     RawRow<Tin> raw[RPW + 1];

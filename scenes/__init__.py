@@ -221,3 +221,37 @@ def uneven_pair_sizes(n: int, seed: int, wmin=160, wmax=1920, hmin=120, hmax=108
     Z0 = rng.uniform(5.0, 50.0, size=n)
     sp = rng.uniform(0.01, 0.2, size=n)
     return [(int(h), int(w), float(z), float(s)) for h, w, z, s in zip(H, W, Z0, sp)]
+
+
+# camera streams for the serving workload: 16 streams each of 320x240, 640x480,
+# 1280x720 and 1920x1080 (H, W)
+CAMERA_CLASSES = ((240, 320), (480, 640), (720, 1280), (1080, 1920))
+
+
+def camera_streams(per_class: int = 16, classes=CAMERA_CLASSES, seed: int = 0):
+    """Seeded stream specs [(sid, H, W, scene_seed, Z0, speed)], classes interleaved."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(per_class):
+        for H, W in classes:
+            sid = len(out)
+            out.append((sid, H, W, int(seed * 1000003 + sid), float(rng.uniform(10.0, 40.0)),
+                        float(rng.uniform(0.02, 0.1))))
+    return out
+
+
+def poisson_arrivals(n_streams: int, fps: float, duration_s: float, seed: int):
+    """Frame arrival times of independent streams: exponential inter-arrival times of
+    mean 1/fps, each stream starting at a random phase.  Returns a time-sorted list of
+    (t_seconds, stream, seq)."""
+    rng = np.random.default_rng(seed)
+    ev = []
+    for s in range(n_streams):
+        t = float(rng.uniform(0.0, 1.0 / fps))
+        seq = 0
+        while t < duration_s:
+            ev.append((t, s, seq))
+            seq += 1
+            t += float(rng.exponential(1.0 / fps))
+    ev.sort()
+    return ev

@@ -137,3 +137,31 @@ def test_result_layout_matches_header():
     assert "double sums[10];" in text
     assert ft.RESULT_DTYPE.itemsize == 152
     assert ft.RESULT_DTYPE.fields["n"][1] == 136 and ft.RESULT_DTYPE.fields["flags"][1] == 148
+
+
+def test_pyramid_layout_and_pair_desc(L):
+    """Pyramid blocks: level l of floor(H/2^l) x floor(W/2^l) pixels, uint16 for
+    uint8 frames up to level 4 and float beyond, rows padded to 16 bytes, images
+    aligned to 256 bytes; the descriptor mirrors the header's struct."""
+    lay = ft.pyramid_layout(1080, 1920, 6)
+    es = [0, 2, 2, 2, 2, 4]
+    off = 0
+    for l in range(1, 6):
+        w, h = 1920 >> l, 1080 >> l
+        assert lay["pitches"][l] == -(-(w * es[l]) // 16) * 16
+        assert lay["offsets"][l] == off
+        off += -(-(lay["pitches"][l] * h) // 256) * 256
+    assert lay["bytes"] == off
+    assert ft.pyramid_layout(100, 100, 1)["bytes"] == 0
+    f32 = ft.pyramid_layout(33, 70, 2, dtype=__import__("torch").float32)
+    assert f32["pitches"][1] == 144 and f32["bytes"] == 256 * -(-(144 * 16) // 256)
+    b = ctypes.c_int64()
+    assert L.ttc_pyramid_layout(8, 8, 4, 0, None, None, ctypes.byref(b)) == 2        # level 3 is 1 x 1
+    assert L.ttc_pyramid_layout(64, 64, 8, 0, None, None, ctypes.byref(b)) == 3
+    assert L.ttc_pyramid_layout(64, 64, 2, 5, None, None, ctypes.byref(b)) == 1
+    assert L.ttc_pyramid_layout(64, 64, 2, 0, None, None, None) == 1
+    rows = (ctypes.c_int * 2)(64, 16)
+    assert L.ttc_batch_set_plan(None, rows, 2) == 1
+    text = open(os.path.join(ROOT, "include", "fastttc.h")).read()
+    assert "const void *prev_pyramid;" in text and "void *cur_pyramid;" in text
+    assert ctypes.sizeof(ft.PairDesc) == 48 and ft.PairDesc.cur_pyramid.offset == 40

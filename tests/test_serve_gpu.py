@@ -1,0 +1,183 @@
+"""Serving path on the GPU: caller-owned per-frame pyramids in the batch API, and the
+serving loop over the batch engine (results vs the oracle, identical alone and in a
+mix of streams, host-side faults)."""
+import collections
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1612_08825_gb300 as ft
+import scenes
+from _tol import check_record
+from paper_1612_08825_gb300.serve import CudaBatchEngine, Frame, PerFrameEngine, Server, replay, saturate
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda")
+LEVELS = 4
+PLAN = [64, 64, 16, 16]
+
+
+def _video(H, W, n, seed):
+    sc = scenes.tilted_plane_scene(H=H, W=W, seed=seed, Z0=18.0, speed=0.06, m=16, pmin=3.0, pmax=40.0)
+    return scenes.render_sequence(sc, n, device=DEV).cpu()
+
+
+SIZES = [(120, 160), (243, 337), (480, 640), (1080, 1920), (35, 71)]
+
+
+def _pyr_level(block, lay, l, H, W):
+    off, pitch = lay["offsets"][l], lay["pitches"][l]
+    h, w = H >> l, W >> l
+    raw = block[off:off + pitch * h].view(h, pitch)[:, :2 * w].contiguous()
+    return raw.view(torch.int16).to(torch.int32).cpu().numpy() & 0xFFFF
+
+
+def test_pyramid_layout_and_plan_errors():
+    lay = ft.pyramid_layout(1080, 1920, 4)
+    assert lay["pitches"][1:] == [1920, 960, 480]
+    assert lay["bytes"] == sum(((lay["pitches"][l] * (1080 >> l) + 255) // 256) * 256 for l in (1, 2, 3))
+    with pytest.raises(ft.FtError):
+        ft.pyramid_layout(12, 12, 4)                       # level 3 would be 1 x 1
+    ctx = ft.TtcContext(64, 64, 3, 2)
+    with pytest.raises(ft.FtError):
+        ctx.batch_set_plan([64, 32, 16])
+    ctx.batch_set_plan([64, 16, 16])
+    ctx.batch_set_plan(None)
+    ctx.close()
+
+
+def test_caller_pyramids_same_as_context_pyramids():
+    """Pairs (f0, f1) then (f1, f2) with the pyramids in caller blocks (f1's built
+    once, by the first pair, and read by the second) give bitwise the records of the
+    same pairs with context pyramids; the stored levels are the exact block sums."""
+    vids = [_video(H, W, 3, 50 + i) for i, (H, W) in enumerate(SIZES)]
+    dev = [v.to(DEV) for v in vids]
+    n = len(SIZES)
+    ctx = ft.TtcContext(1080, 1920, LEVELS, 2 * n)
+    ctx.batch_set_plan(PLAN)
+    ctx.batch_prepare([(d[0], d[1]) for d in dev] + [(d[1], d[2]) for d in dev], levels=LEVELS)
+    ref = ft.results_to_numpy(ctx.batch_run(mode=1)).reshape(2, n, LEVELS)
+    lays = [ft.pyramid_layout(H, W, LEVELS) for H, W in SIZES]
+    blocks = [torch.full((2, max(l["bytes"], 256)), 0xAB, dtype=torch.uint8, device=DEV) for l in lays]
+    ctx.batch_prepare([(d[0], d[1], None, b[0]) for d, b in zip(dev, blocks)], levels=LEVELS)
+    first = ft.results_to_numpy(ctx.batch_run(mode=1)).reshape(n, LEVELS)
+    ctx.batch_prepare([(d[1], d[2], b[0], b[1]) for d, b in zip(dev, blocks)], levels=LEVELS)
+    second = ft.results_to_numpy(ctx.batch_run(mode=1)).reshape(n, LEVELS)
+    torch.cuda.synchronize()
+    assert first.tobytes() == ref[0].tobytes()
+    assert second.tobytes() == ref[1].tobytes()
+    for i, (H, W) in enumerate(SIZES):
+        for k, frame in ((0, vids[i][1]), (1, vids[i][2])):
+            img = frame.numpy().astype(np.float64)
+            for l in range(1, LEVELS):
+                img = oracle.downsample(img)
+                got = _pyr_level(blocks[i][k], lays[i], l, H, W)
+                assert np.array_equal(got, (img * 4 ** l).astype(np.int64)), (H, W, k, l)
+        if (H, W) == (1080, 1920):
+            continue
+        for p in range(2):
+            r = oracle.ttc_pair(vids[i][p].numpy(), vids[i][p + 1].numpy(), levels=LEVELS, mode=1)
+            for l in range(LEVELS):
+                check_record((first, second)[p][i, l], r[l], 1, l)
+    ctx.close()
+
+
+def test_misaligned_pyramid_rejected():
+    v = _video(64, 96, 2, 7).to(DEV)
+    ctx = ft.TtcContext(64, 96, 3, 1)
+    blk = torch.zeros(4096, dtype=torch.uint8, device=DEV)
+    with pytest.raises(ft.FtError):
+        ctx.batch_prepare([(v[0], v[1], None, blk[8:])], levels=3)
+    with pytest.raises(ft.FtError):
+        ctx.batch_prepare([(v[0], v[1], blk, blk)], levels=3)
+    ctx.close()
+
+
+STREAMS = [(0, 120, 160), (1, 480, 640), (2, 243, 337), (3, 1080, 1920), (4, 240, 320), (5, 35, 71)]
+NFR = 5
+
+
+def _serve(streams, frames, engine_kind="batch", remove_at=None):
+    if engine_kind == "batch":
+        eng = CudaBatchEngine(1080, 1920, LEVELS, max_batch=8, rows_per_tile=PLAN)
+    else:
+        eng = PerFrameEngine(1080, 1920, LEVELS)
+    srv = Server(eng, 40 << 30, max_batch=8)
+    for sid, H, W in streams:
+        assert srv.admit(sid, H, W)
+    done = []
+    for k in range(NFR):
+        for sid, _, _ in streams:
+            if remove_at is not None and (sid, k) == remove_at:
+                srv.remove(sid)
+            srv.offer(Frame(sid, k, float(k), frames[sid][k]))
+        done += srv.step()
+    done += srv.drain()
+    return done, srv
+
+
+def test_server_results_oracle_and_mix_invariance():
+    frames = {sid: _video(H, W, NFR, 200 + sid).pin_memory() for sid, H, W in STREAMS}
+    mix, srv = _serve(STREAMS, frames)
+    assert srv.stats["results"] == len(STREAMS) * (NFR - 1) and srv.stats["first_frames"] == len(STREAMS)
+    by = {(c.stream, c.seq): c for c in mix}
+    for sid, H, W in STREAMS:
+        alone, _ = _serve([(sid, H, W)], frames)
+        for c in alone:
+            m = by[(sid, c.seq)]
+            if c.records is None:
+                assert m.records is None
+                continue
+            assert m.records.tobytes() == c.records.tobytes(), (sid, c.seq)
+            assert m.level == c.level
+        if H * W > 500_000:
+            continue
+        for k in range(1, NFR):
+            r = oracle.ttc_pair(frames[sid][k - 1].numpy(), frames[sid][k].numpy(), levels=LEVELS, mode=1)
+            for l in range(LEVELS):
+                check_record(by[(sid, k)].records[l], r[l], 1, l)
+
+
+def test_server_stream_removed_mid_flight_others_unchanged():
+    frames = {sid: _video(H, W, NFR, 400 + sid).pin_memory() for sid, H, W in STREAMS}
+    full, _ = _serve(STREAMS, frames)
+    cut, srv = _serve(STREAMS, frames, remove_at=(3, 2))
+    assert all(c.stream != 3 or c.seq < 2 for c in cut)
+    assert 3 not in srv.streams
+    ref = {(c.stream, c.seq): c.records for c in full}
+    for c in cut:
+        if c.records is not None:
+            assert c.records.tobytes() == ref[(c.stream, c.seq)].tobytes()
+
+
+def test_per_frame_engine_matches_batch_engine():
+    frames = {sid: _video(H, W, NFR, 600 + sid).pin_memory() for sid, H, W in STREAMS[:3]}
+    a, _ = _serve(STREAMS[:3], frames)
+    b, _ = _serve(STREAMS[:3], frames, engine_kind="per_frame")
+    ra = {(c.stream, c.seq): c.records for c in a if c.records is not None}
+    for c in b:
+        if c.records is None:
+            continue
+        r = oracle.ttc_pair(frames[c.stream][c.seq - 1].numpy(), frames[c.stream][c.seq].numpy(),
+                            levels=LEVELS, mode=1)
+        for l in range(LEVELS):
+            check_record(c.records[l], r[l], 1, l)
+            check_record(ra[(c.stream, c.seq)][l], r[l], 1, l)
+
+
+def test_replay_and_saturate_on_gpu():
+    frames = {sid: _video(H, W, 3, 800 + sid).pin_memory() for sid, H, W in STREAMS}
+    eng = CudaBatchEngine(1080, 1920, LEVELS, max_batch=8, rows_per_tile=PLAN)
+    srv = Server(eng, 40 << 30, max_batch=8)
+    for sid, H, W in STREAMS:
+        srv.admit(sid, H, W)
+    arr = scenes.poisson_arrivals(len(STREAMS), 200.0, 0.05, seed=3)
+    done = replay(srv, arr, lambda s, q: frames[s][q % 3])
+    assert len(done) == len(arr) - srv.stats["dropped_frames"]
+    assert all(c.latency >= 0 for c in done)
+    n0 = srv.stats["results"]
+    saturate(srv, lambda s, q: frames[s][q % 3], ticks=6)
+    assert srv.stats["results"] - n0 >= 5 * len(STREAMS)
+    assert eng.launches > 0
