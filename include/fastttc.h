@@ -35,7 +35,8 @@ typedef enum {
     FT_ERR_SHAPE = 2,         /* dimensions inconsistent or too small for the request */
     FT_ERR_UNSUPPORTED = 3,   /* valid request beyond this build's limits */
     FT_ERR_WORKSPACE = 4,     /* request larger than the context was created for */
-    FT_ERR_CUDA = 5           /* a CUDA runtime call failed */
+    FT_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    FT_ERR_TIMEOUT = 6        /* a bounded wait inside a kernel gave up (see fastconv_check) */
 } ft_status;
 
 #define FT_MAX_NDIM 8         /* fastconv_nd: largest rank */
@@ -72,11 +73,22 @@ ft_status fastconv_out_dims(int nd, const int64_t *dims, const int64_t *kdims, i
  *   out    : device, prod(dims + kdims - 1) floats; every element is written.
  *   nd     : rank, 1 <= nd <= FT_MAX_NDIM.
  * Accumulation is FP32 in a fixed order.  input/kernel must not overlap out.
+ * Some kernels receive their input tiles from the copy engine and wait for them with
+ * a time limit; a wait that gives up leaves part of `out` unwritten and is reported by
+ * the next fastconv_check.
  * Errors: FT_ERR_INVALID_ARG, FT_ERR_SHAPE, FT_ERR_UNSUPPORTED (output or kernel
  * with more than 2^62 elements), FT_ERR_CUDA.
  */
 ft_status fastconv_nd(const float *input, const int64_t *dims, int nd,
                       const float *kernel, const int64_t *kdims, float *out, void *stream);
+
+/*
+ * Synchronises `stream`, then reports (and clears) the device-wide FastConv status
+ * word of the current device: FT_ERR_TIMEOUT if a bounded wait of a FastConv kernel
+ * gave up since the last check (its output is incomplete), FT_OK otherwise.  No
+ * counterpart in the paper.  Errors: FT_ERR_CUDA.
+ */
+ft_status fastconv_check(void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Time to contact (Sec. V-A, V-B)                                           */

@@ -20,7 +20,8 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "ttc_derivatives", "ttc_solve_noalloc",
+    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "fastconv_check", "ttc_derivatives",
+    "ttc_solve_noalloc",
     "TtcContext", "RESULT_DTYPE", "results_to_numpy", "select_level",
     "MODE_TTC", "MODE_FOE", "FLAG_SINGULAR", "FLAG_C_ZERO", "FLAG_RECEDING", "MAX_LEVELS",
     "MAX_NDIM",
@@ -84,6 +85,8 @@ def load(path: Optional[str] = None):
     L.fastconv_out_dims.restype = st
     L.fastconv_nd.argtypes = [_vp, _i64p, ctypes.c_int, _vp, _i64p, _vp, _vp]
     L.fastconv_nd.restype = st
+    L.fastconv_check.argtypes = [_vp]
+    L.fastconv_check.restype = st
     L.ttc_derivatives.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                   _vp, _vp, _vp, _vp, _vp]
     L.ttc_derivatives.restype = st
@@ -184,6 +187,13 @@ def fastconv_nd(x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = 
     _check(L.fastconv_nd(x.data_ptr(), _dims(x.shape), x.dim(), k.data_ptr(), _dims(k.shape),
                          out.data_ptr(), _stream_ptr(x)), "fastconv_nd")
     return out
+
+
+def fastconv_check(device=None):
+    """Synchronise the current stream; raise FtError if a FastConv wait gave up since the last check."""
+    L = load()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    _check(L.fastconv_check(torch.cuda.current_stream(dev).cuda_stream), "fastconv_check")
 
 
 # --------------------------------------------------------------------------- #

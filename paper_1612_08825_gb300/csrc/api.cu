@@ -1,7 +1,9 @@
 // Status strings, version and CUDA-error bookkeeping of the fastttc C ABI.
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace ft {
 
@@ -12,6 +14,22 @@ void set_cuda_error(cudaError_t e)
     const char *s = cudaGetErrorString(e);
     std::strncpy(g_cuda_error, s ? s : "unknown CUDA error", sizeof(g_cuda_error) - 1);
     g_cuda_error[sizeof(g_cuda_error) - 1] = '\0';
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        cudaGetLastError();
+    });
+    return fn;
 }
 
 }  // namespace ft
@@ -25,6 +43,7 @@ extern "C" const char *ft_status_string(int status)
     case FT_ERR_UNSUPPORTED: return "FT_ERR_UNSUPPORTED";
     case FT_ERR_WORKSPACE: return "FT_ERR_WORKSPACE";
     case FT_ERR_CUDA: return "FT_ERR_CUDA";
+    case FT_ERR_TIMEOUT: return "FT_ERR_TIMEOUT";
     default: return "FT_ERR_UNKNOWN";
     }
 }

@@ -14,9 +14,18 @@
 // (float4 shared loads, conflict-free).  The output tile goes back through shared
 // memory so that global stores are fully coalesced 128-byte rows whatever the
 // alignment of the output row length.  Accumulation is FP32 FMA in a fixed order.
+//
+// FMA-bound plane kernels (4..129 rows, up to 17 columns) use conv_fma_kernel instead:
+// asynchronous zero-filling copies for the staging and a branch-free schedule of the
+// multiply-adds.
+#include <algorithm>
 #include <cstdio>
 
 #include "common.cuh"
+#include "tma.cuh"
+
+// set to 1 when a wait of a TMA-fed FastConv kernel gave up (read by fastconv_check)
+__device__ int g_fastconv_status;
 
 namespace {
 
@@ -51,7 +60,9 @@ conv_tile_kernel(const ConvParams p)
 
     const int Kr = (int)p.Kr, Kc = (int)p.Kc;
     const int SH = TH + Kr - 1;
-    float *ks = sm + SH * SW;            // kernel slice, Kr * Kc floats
+    const int KS = (Kc + 3) & ~3;        // kernel row stride in shared memory (zero-padded)
+    float *ks = sm + SH * SW;            // kernel slice, Kr * KS floats
+    const float4 *ks4 = reinterpret_cast<const float4 *>(ks);
 
     const int tid = threadIdx.x;
     const int64_t bid = blockIdx.x;
@@ -98,7 +109,10 @@ conv_tile_kernel(const ConvParams p)
 
         const float *src = p.in + q * p.Nr * p.Nc;
         const float *kk = p.ker + R * p.Kr * p.Kc;
-        for (int i = tid; i < Kr * Kc; i += kThreads) ks[i] = __ldg(kk + i);
+        for (int i = tid; i < Kr * KS; i += kThreads) {
+            const int a = i / KS, b = i - a * KS;
+            ks[i] = b < Kc ? __ldg(kk + a * Kc + b) : 0.f;
+        }
 
         const int64_t iy0 = oy0 - (Kr - 1), ix0 = ox0 - PADC;
         if (p.vec_in) {
@@ -134,17 +148,25 @@ conv_tile_kernel(const ConvParams p)
                 win[4 * v + 2] = f.z;
                 win[4 * v + 3] = f.w;
             }
+            // kernel taps four at a time (one broadcast 16-byte shared load feeds 16
+            // FMAs); taps past Kc are zero in shared memory
 #pragma unroll
             for (int y = 0; y < OY; ++y) {
                 const int a = y + Kr - 1 - ir;
                 if (a < 0 || a >= Kr) continue;
-                const float *krow = ks + a * Kc;
+                const float4 *krow = ks4 + a * (KS / 4);
 #pragma unroll
-                for (int b = 0; b <= PADC; ++b) {
-                    if (b >= Kc) break;
-                    const float kv = krow[b];
+                for (int b4 = 0; b4 <= PADC / 4; ++b4) {
+                    if (4 * b4 >= Kc) break;
+                    const float4 k4 = krow[b4];
+                    const float kv[4] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[y][c] = fmaf(kv, win[c - b + PADC], acc[y][c]);
+                    for (int j = 0; j < 4; ++j) {
+                        const int b = 4 * b4 + j;
+                        if (b > PADC) break;     // compile time: tap b reads window index c - b + PADC
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[y][c] = fmaf(kv[j], win[c - b + PADC], acc[y][c]);
+                    }
                 }
             }
         }
@@ -163,6 +185,203 @@ conv_tile_kernel(const ConvParams p)
     for (int i = tid; i < TH * TW; i += kThreads) {
         const int r = i / TW, c = i - r * TW;
         if (r < rows && c < cols) dst[(oy0 + r) * p.Mc + ox0 + c] = sm[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FMA-bound plane kernel (kernels of 4..17 rows and up to 17 columns)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+
+// 16-byte asynchronous global -> shared copy; bytes = 0 writes zeros and reads nothing
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// the NTAP taps of one kernel row (float4 groups in shared memory) applied to one
+// output row's four columns from the thread's window: acc[c] += k[b] * in[c - b]
+template <int NTAP, int PADC>
+__device__ __forceinline__ void fma_row(float (&acc)[4], const float (&win)[PADC + 4], const float4 *krow)
+{
+#pragma unroll
+    for (int g = 0; g < (NTAP + 3) / 4; ++g) {
+        const float4 k4 = krow[g];
+        const float kv[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int b = 4 * g + j;
+            if (b < NTAP) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[c] = fmaf(kv[j], win[c - b + PADC], acc[c]);
+            }
+        }
+    }
+}
+
+template <int PADC>
+__device__ __forceinline__ void load_window(float (&win)[PADC + 4], const float *row)
+{
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+    for (int v = 0; v < (PADC + 4) / 4; ++v) {
+        const float4 f = r4[v];
+        win[4 * v + 0] = f.x;
+        win[4 * v + 1] = f.y;
+        win[4 * v + 2] = f.z;
+        win[4 * v + 3] = f.w;
+    }
+}
+
+// A CTA owns TH = 8 * OY output rows x 128 columns; thread (warp w, lane l) computes
+// rows OY * w .. + OY - 1 and columns 4l .. 4l + 3.  The zero-padded input tile
+// arrives by cp.async (out-of-image 16-byte groups are zero-filled by the copy, so
+// every copy of the tile is in flight at once) and the kernel slice is stored with
+// rows zero-padded to whole float4 groups.  Staged input row ir (0 .. OY + Kr - 2 for
+// the thread) feeds output row y through kernel row a = y + Kr - 1 - ir; with
+// Kr >= OY the valid (ir, y) pairs form three phases whose bounds are known at
+// compile time except for the middle one's length (rows OY - 1 .. Kr - 1, where
+// every output row is fed), so the multiply-add stream has no branches: each window
+// of PADC + 4 floats is loaded once and one broadcast 16-byte load of the kernel feeds
+// 16 FMAs.  Order per output: input rows ascending, taps ascending (FP32 FMA).
+template <int NTAP, int OY>
+__global__ void __launch_bounds__(kThreads, OY == 8 ? 2 : 3)
+conv_fma_kernel(const ConvParams p)
+{
+    constexpr int PADC = (NTAP - 1 + 3) & ~3;
+    constexpr int TW = 128;
+    constexpr int TH = 8 * OY;
+    constexpr int SW = TW + PADC;
+    constexpr int SW4 = SW / 4;
+    constexpr int KS = (NTAP + 3) & ~3;  // kernel row stride, floats
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+
+    const int Kr = (int)p.Kr, Kc = (int)p.Kc;
+    const int SH = TH + Kr - 1;
+    float *ks = sm + SH * SW;
+    const float4 *ks4 = reinterpret_cast<const float4 *>(ks);
+
+    const int tid = threadIdx.x;
+    const int64_t bid = blockIdx.x;
+    const int64_t plane = bid / p.tiles_per_plane;
+    const int64_t t = bid - plane * p.tiles_per_plane;
+    const int64_t ty = t / p.tiles_x;
+    const int64_t tx = t - ty * p.tiles_x;
+    const int64_t oy0 = ty * TH, ox0 = tx * TW;
+
+    int64_t pm[FT_MAX_NDIM];
+    {
+        int64_t r = plane;
+        for (int d = p.nlead - 1; d >= 0; --d) {
+            pm[d] = r % p.out_lead[d];
+            r /= p.out_lead[d];
+        }
+    }
+
+    const int c0 = 4 * (tid & 31);
+    const int r0 = OY * (tid >> 5);
+    float acc[OY][4];
+#pragma unroll
+    for (int y = 0; y < OY; ++y)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[y][c] = 0.f;
+
+    bool first = true;
+    for (int64_t R = 0; R < p.k_lead_total; ++R) {
+        int64_t q = 0, rr = R, stride = 1;
+        bool inside = true;
+        for (int d = p.nlead - 1; d >= 0; --d) {
+            int64_t rd = rr % p.k_lead[d];
+            rr /= p.k_lead[d];
+            int64_t qd = pm[d] - rd;
+            if (qd < 0 || qd >= p.in_lead[d]) inside = false;
+            q += qd * stride;
+            stride *= p.in_lead[d];
+        }
+        if (!inside) continue;           // uniform over the CTA
+        if (!first) __syncthreads();
+        first = false;
+
+        const float *src = p.in + q * p.Nr * p.Nc;
+        const float *kk = p.ker + R * p.Kr * p.Kc;
+        for (int i = tid; i < Kr * KS; i += kThreads) {
+            const int a = i / KS, b = i - a * KS;
+            ks[i] = b < Kc ? __ldg(kk + a * Kc + b) : 0.f;
+        }
+        const int64_t iy0 = oy0 - (Kr - 1), ix0 = ox0 - PADC;
+        if (p.vec_in) {
+            for (int i = tid; i < SH * SW4; i += kThreads) {
+                const int r = i / SW4, c4 = i - r * SW4;
+                const int64_t gy = iy0 + r, gx = ix0 + 4 * c4;
+                const bool ok = gy >= 0 && gy < p.Nr && gx >= 0 && gx < p.Nc;
+                cp_async16(smem4 + i, ok ? src + gy * p.Nc + gx : src, ok ? 16 : 0);
+            }
+            cp_async_wait_all();
+        } else {
+            for (int i = tid; i < SH * SW; i += kThreads) {
+                const int r = i / SW, c = i - r * SW;
+                const int64_t gy = iy0 + r, gx = ix0 + c;
+                float v = 0.f;
+                if (gy >= 0 && gy < p.Nr && gx >= 0 && gx < p.Nc) v = __ldg(src + gy * p.Nc + gx);
+                sm[i] = v;
+            }
+        }
+        __syncthreads();
+
+        const float *base = sm + r0 * SW + c0;
+        float win[PADC + 4];
+        // phase 1: input rows 0 .. OY - 2 feed output rows 0 .. ir
+#pragma unroll
+        for (int ir = 0; ir < OY - 1; ++ir) {
+            load_window<PADC>(win, base + ir * SW);
+#pragma unroll
+            for (int y = 0; y <= ir; ++y) fma_row<NTAP, PADC>(acc[y], win, ks4 + (y + Kr - 1 - ir) * (KS / 4));
+        }
+        // phase 2: input rows OY - 1 .. Kr - 1 feed every output row
+        for (int ir = OY - 1; ir < Kr; ++ir) {
+            load_window<PADC>(win, base + ir * SW);
+            const float4 *kb = ks4 + (Kr - 1 - ir) * (KS / 4);
+#pragma unroll
+            for (int y = 0; y < OY; ++y) fma_row<NTAP, PADC>(acc[y], win, kb + y * (KS / 4));
+        }
+        // phase 3: input rows Kr - 1 + t, t = 1 .. OY - 1, feed output rows t .. OY - 1
+#pragma unroll
+        for (int t3 = 1; t3 < OY; ++t3) {
+            load_window<PADC>(win, base + (Kr - 1 + t3) * SW);
+#pragma unroll
+            for (int y = t3; y < OY; ++y) fma_row<NTAP, PADC>(acc[y], win, ks4 + (y - t3) * (KS / 4));
+        }
+    }
+
+    // stage the output tile in shared memory, then store coalesced rows
+    __syncthreads();
+#pragma unroll
+    for (int y = 0; y < OY; ++y)
+        *reinterpret_cast<float4 *>(sm + (r0 + y) * TW + c0) = make_float4(acc[y][0], acc[y][1], acc[y][2], acc[y][3]);
+    __syncthreads();
+    float *dst = p.out + plane * p.Mr * p.Mc;
+    const int64_t rows = p.Mr - oy0 < TH ? p.Mr - oy0 : TH;
+    const int64_t cols = p.Mc - ox0 < TW ? p.Mc - ox0 : TW;
+    if (p.vec_out) {
+        for (int i = tid; i < TH * TW / 4; i += kThreads) {
+            const int r = i / (TW / 4), c = 4 * (i - r * (TW / 4));
+            if (r < rows && c < cols)
+                *reinterpret_cast<float4 *>(dst + (oy0 + r) * p.Mc + ox0 + c) =
+                    *reinterpret_cast<const float4 *>(sm + r * TW + c);
+        }
+    } else {
+        for (int i = tid; i < TH * TW; i += kThreads) {
+            const int r = i / TW, c = i - r * TW;
+            if (r < rows && c < cols) dst[(oy0 + r) * p.Mc + ox0 + c] = sm[i];
+        }
     }
 }
 
@@ -374,7 +593,7 @@ ft_status launch_tile(const ConvParams &p0, int64_t planes, cudaStream_t s)
     p.tiles_per_plane = tiles_y * p.tiles_x;
     const int64_t blocks = planes * p.tiles_per_plane;
     if (blocks > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
-    const size_t smem = sizeof(float) * ((size_t)(TH + p.Kr - 1) * (TW + PADC) + (size_t)(p.Kr * p.Kc));
+    const size_t smem = sizeof(float) * ((size_t)(TH + p.Kr - 1) * (TW + PADC) + (size_t)(p.Kr * ((p.Kc + 3) & ~3)));
     if (smem > 48 * 1024) {              // opt-in above 48 KB (current device)
         cudaError_t e = cudaFuncSetAttribute(conv_tile_kernel<PADC, OY, WX>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -386,6 +605,362 @@ ft_status launch_tile(const ConvParams &p0, int64_t planes, cudaStream_t s)
     }
     conv_tile_kernel<PADC, OY, WX><<<(unsigned)blocks, kThreads, smem, s>>>(p);
     return ft::check_launch();
+}
+
+template <int NTAP, int OY>
+ft_status launch_fma(const ConvParams &p0, int64_t planes, cudaStream_t s)
+{
+    constexpr int PADC = (NTAP - 1 + 3) & ~3;
+    constexpr int TW = 128, TH = 8 * OY;
+    ConvParams p = p0;
+    const int64_t tiles_y = ft::ceil_div(p.Mr, TH);
+    p.tiles_x = ft::ceil_div(p.Mc, TW);
+    p.tiles_per_plane = tiles_y * p.tiles_x;
+    const int64_t blocks = planes * p.tiles_per_plane;
+    if (blocks > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
+    const size_t smem =
+        sizeof(float) * ((size_t)(TH + p.Kr - 1) * (TW + PADC) + (size_t)p.Kr * ((NTAP + 3) & ~3));
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(conv_fma_kernel<NTAP, OY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) {
+            ft::set_cuda_error(e);
+            return FT_ERR_CUDA;
+        }
+    }
+    conv_fma_kernel<NTAP, OY><<<(unsigned)blocks, kThreads, smem, s>>>(p);
+    return ft::check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// persistent FMA-bound kernel fed by the Tensor Memory Accelerator
+// ---------------------------------------------------------------------------
+
+// input plane feeding output plane `plane` through leading kernel index R, or -1 when
+// it lies outside the input (ranks <= 3 need no division)
+__device__ __forceinline__ int64_t lead_plane(const ConvParams &p, int64_t plane, int64_t R)
+{
+    if (p.nlead == 0) return 0;
+    if (p.nlead == 1) {
+        const int64_t q = plane - R;
+        return (q >= 0 && q < p.in_lead[0]) ? q : -1;
+    }
+    int64_t q = 0, stride = 1, rp = plane, rr = R;
+    for (int d = p.nlead - 1; d >= 0; --d) {
+        const int64_t pd = rp % p.out_lead[d], rd = rr % p.k_lead[d];
+        rp /= p.out_lead[d];
+        rr /= p.k_lead[d];
+        const int64_t qd = pd - rd;
+        if (qd < 0 || qd >= p.in_lead[d]) return -1;
+        q += qd * stride;
+        stride *= p.in_lead[d];
+    }
+    return q;
+}
+
+namespace conv_tma {
+
+constexpr int OY = 4, TH = 8 * OY, TW = 128;
+
+struct Params {
+    ConvParams p;
+    int planes;                  // output planes
+    int tiles_x, tiles_per_plane;
+    int SH;                      // staged rows per tile: TH + Kr - 1
+    int buf_floats;              // floats per staging buffer (whole 128-byte units)
+    int store_tma;               // 1: output tiles leave by TMA store, 0: by plain stores
+    int *status;                 // set to 1 when a wait gives up
+};
+
+// work items: (plane, tile, R) with tile t of output plane `plane` (the CTA's tiles are
+// blockIdx.x, + gridDim.x, ... over all planes) and leading kernel index R whose input
+// plane q exists
+struct Item {
+    int plane, tile;
+    int64_t R, q;
+};
+
+// the first item at or after `it` (R included)
+__device__ __forceinline__ bool advance(const Params &cp, Item &it)
+{
+    while (it.plane < cp.planes) {
+        for (; it.R < cp.p.k_lead_total; ++it.R) {
+            it.q = lead_plane(cp.p, it.plane, it.R);
+            if (it.q >= 0) return true;
+        }
+        it.R = 0;
+        it.tile += gridDim.x;
+        while (it.tile >= cp.tiles_per_plane && it.plane < cp.planes) {
+            it.tile -= cp.tiles_per_plane;
+            ++it.plane;
+        }
+    }
+    return false;
+}
+
+// elected thread: the staged box of item (t, q) into `buf` (rows oy0 - (Kr - 1) ..,
+// columns ox0 - PADC ..; the copy engine zero-fills outside the input)
+template <int PADC>
+__device__ __forceinline__ void issue(const CUtensorMap *m, const Params &cp, const Item &it, float *buf,
+                                      uint64_t *bar)
+{
+    const int ty = it.tile / cp.tiles_x, tx = it.tile - ty * cp.tiles_x;
+    ft_tma::fence_proxy_async();
+    ft_tma::mbar_expect_tx(bar, (uint32_t)(cp.SH * (TW + PADC) * 4));
+    ft_tma::tma_load_3d(buf, m, tx * TW - PADC, ty * TH - ((int)cp.p.Kr - 1), (int)it.q, bar);
+}
+
+// A CTA walks tiles blockIdx.x, + gridDim.x, ... and, for each, the leading kernel
+// indices whose input plane exists (one work item each).  One elected thread brings the
+// next item's box into the other of two staging buffers while the CTA computes the
+// current one (completion tracked by an mbarrier with the box's byte count), so the
+// copies overlap the FMAs.  The arithmetic per item is that of conv_fma_kernel (three
+// branch-free phases of staged rows, OY rows x 4 columns per thread, kernel taps four
+// at a time from shared memory); all kernel slices are staged once.  Finished tiles go
+// out through a shared-memory staging tile, by TMA store when the output rows allow it.
+// Every wait is bounded: on expiry the CTA sets the status word, waits a bounded time
+// for its copy in flight, and returns.
+template <int NTAP>
+__global__ void __launch_bounds__(kThreads, NTAP <= 9 ? 3 : 2)
+conv_tma_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_map,
+                const Params cp)
+{
+    constexpr int PADC = (NTAP - 1 + 3) & ~3;
+    constexpr int BW = TW + PADC;
+    constexpr int KS = (NTAP + 3) & ~3;
+    extern __shared__ __align__(128) float smf[];
+    const ConvParams &p = cp.p;
+    const int tid = threadIdx.x;
+    const int Kr = (int)p.Kr, Kc = (int)p.Kc;
+    float *buf0 = smf, *buf1 = smf + cp.buf_floats;
+    float *so = smf + 2 * cp.buf_floats;
+    float *ks = so + TH * TW;
+    const int nk = (int)p.k_lead_total * Kr * KS;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ks + ((nk + 3) & ~3));
+    // the copy engine writes 128-byte aligned boxes; refuse (and report) otherwise
+    if (ft_tma::smem_addr(smf) & 127) {
+        if (tid == 0) atomicExch(cp.status, 2);
+        return;
+    }
+    for (int i = tid; i < nk; i += kThreads) {
+        const int row = i / KS, b = i - row * KS;      // row = R * Kr + a
+        ks[i] = b < Kc ? __ldg(p.ker + (int64_t)row * Kc + b) : 0.f;
+    }
+    if (tid == 0) {
+        ft_tma::mbar_init(&bar[0], 1);
+        ft_tma::mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    Item it{0, (int)blockIdx.x, 0, 0};
+    while (it.tile >= cp.tiles_per_plane && it.plane < cp.planes) {
+        it.tile -= cp.tiles_per_plane;
+        ++it.plane;
+    }
+    bool have = advance(cp, it);
+    if (tid == 0 && have) issue<PADC>(&in_map, cp, it, buf0, &bar[0]);
+
+    const int c0 = 4 * (tid & 31);
+    const int r0 = OY * (tid >> 5);
+    float acc[OY][4];
+#pragma unroll
+    for (int y = 0; y < OY; ++y)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[y][c] = 0.f;
+
+    for (int k = 0; have; ++k) {
+        Item nx = it;
+        ++nx.R;
+        const bool hn = advance(cp, nx);
+        float *cur = (k & 1) ? buf1 : buf0;
+        // the other buffer was released by the barrier that ended the previous item
+        if (tid == 0 && hn) issue<PADC>(&in_map, cp, nx, (k & 1) ? buf0 : buf1, &bar[(k + 1) & 1]);
+        const bool ok = ft_tma::mbar_wait(&bar[k & 1], (k >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(cp.status, 1);
+                if (hn) ft_tma::mbar_wait(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1);
+                if (cp.store_tma) ft_tma::bulk_wait();
+            }
+            __syncthreads();
+            return;
+        }
+
+        const float4 *ks4 = reinterpret_cast<const float4 *>(ks + (int64_t)it.R * Kr * KS);
+        const float *base = cur + r0 * BW + c0;
+        float win[PADC + 4];
+#pragma unroll
+        for (int ir = 0; ir < OY - 1; ++ir) {
+            load_window<PADC>(win, base + ir * BW);
+#pragma unroll
+            for (int y = 0; y <= ir; ++y) fma_row<NTAP, PADC>(acc[y], win, ks4 + (y + Kr - 1 - ir) * (KS / 4));
+        }
+        for (int ir = OY - 1; ir < Kr; ++ir) {
+            load_window<PADC>(win, base + ir * BW);
+            const float4 *kb = ks4 + (Kr - 1 - ir) * (KS / 4);
+#pragma unroll
+            for (int y = 0; y < OY; ++y) fma_row<NTAP, PADC>(acc[y], win, kb + y * (KS / 4));
+        }
+#pragma unroll
+        for (int t3 = 1; t3 < OY; ++t3) {
+            load_window<PADC>(win, base + (Kr - 1 + t3) * BW);
+#pragma unroll
+            for (int y = t3; y < OY; ++y) fma_row<NTAP, PADC>(acc[y], win, ks4 + (y - t3) * (KS / 4));
+        }
+        __syncthreads();          // buffer `cur` is free for the copy issued next
+
+        if (!hn || nx.tile != it.tile || nx.plane != it.plane) {
+            // the tile is complete: out through the staging tile
+            const int plane = it.plane;
+            const int ty = it.tile / cp.tiles_x, tx = it.tile - ty * cp.tiles_x;
+            if (cp.store_tma && tid == 0) ft_tma::bulk_wait_read();   // the previous store has read `so`
+            __syncthreads();
+#pragma unroll
+            for (int y = 0; y < OY; ++y)
+                *reinterpret_cast<float4 *>(so + (r0 + y) * TW + c0) =
+                    make_float4(acc[y][0], acc[y][1], acc[y][2], acc[y][3]);
+            if (cp.store_tma) ft_tma::fence_proxy_async();
+            __syncthreads();
+            if (cp.store_tma) {
+                if (tid == 0) {
+                    ft_tma::tma_store_3d(&out_map, so, tx * TW, ty * TH, plane);
+                    ft_tma::bulk_commit();
+                }
+            } else {
+                // plain stores: a thread keeps one column (pair) and walks rows
+                const int64_t oy0 = (int64_t)ty * TH, ox0 = (int64_t)tx * TW;
+                const int rows = p.Mr - oy0 < TH ? (int)(p.Mr - oy0) : TH;
+                const int cols = p.Mc - ox0 < TW ? (int)(p.Mc - ox0) : TW;
+                float *dst = p.out + ((int64_t)plane * p.Mr + oy0) * p.Mc + ox0;
+                if (cp.store_tma == 0 && (p.Mc & 1) == 0 && (reinterpret_cast<uintptr_t>(p.out) & 7) == 0) {
+                    const int c = 2 * (tid & (TW / 2 - 1));
+                    if (c < cols) {
+                        for (int r = tid / (TW / 2); r < rows; r += kThreads / (TW / 2)) {
+                            const float2 v = *reinterpret_cast<const float2 *>(so + r * TW + c);
+                            if (c + 1 < cols) *reinterpret_cast<float2 *>(dst + r * p.Mc + c) = v;
+                            else dst[r * p.Mc + c] = v.x;
+                        }
+                    }
+                } else {
+                    const int c = tid & (TW - 1);
+                    if (c < cols)
+                        for (int r = tid / TW; r < rows; r += kThreads / TW) dst[r * p.Mc + c] = so[r * TW + c];
+                }
+            }
+#pragma unroll
+            for (int y = 0; y < OY; ++y)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[y][c] = 0.f;
+        }
+        it = nx;
+        have = hn;
+    }
+    if (cp.store_tma && tid == 0) ft_tma::bulk_wait();
+}
+
+}  // namespace conv_tma
+
+// 3-D fp32 map over `planes` planes of rows x cols (row-major, contiguous), box
+// bw x bh x 1
+bool f32_plane_map(CUtensorMap *m, const float *base, int64_t cols, int64_t rows, int64_t planes, int bw, int bh)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = ft::tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)(cols * 4), (cuuint64_t)(cols * rows * 4)};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the persistent TMA kernel when the input rows meet the copy engine's rules (16-byte
+// aligned base, row length a multiple of 4 floats) and the staging fits; *used = false
+// otherwise (the caller then takes conv_fma_kernel)
+template <int NTAP>
+ft_status launch_tma(const ConvParams &p, int64_t planes, cudaStream_t s, bool *used)
+{
+    using namespace conv_tma;
+    constexpr int PADC = (NTAP - 1 + 3) & ~3;
+    constexpr int BW = TW + PADC;
+    constexpr int KS = (NTAP + 3) & ~3;
+    *used = false;
+    if (!p.vec_in || p.Kr + TH - 1 > 256) return FT_OK;
+    int64_t in_planes = 1;
+    for (int d = 0; d < p.nlead; ++d) in_planes *= p.in_lead[d];
+    const int64_t tiles_y = ft::ceil_div(p.Mr, TH), tiles_x = ft::ceil_div(p.Mc, TW);
+    if (tiles_y * tiles_x * planes > 0x7fffffffLL) return FT_OK;
+    Params cp{};
+    cp.p = p;
+    cp.planes = (int)planes;
+    cp.tiles_x = (int)tiles_x;
+    cp.tiles_per_plane = (int)(tiles_x * tiles_y);
+    const int64_t total_tiles = planes * cp.tiles_per_plane;
+    cp.SH = TH + (int)p.Kr - 1;
+    cp.buf_floats = (cp.SH * BW + 31) / 32 * 32;
+    const int64_t nk = p.k_lead_total * p.Kr * KS;
+    const size_t smem = sizeof(float) * (2 * (size_t)cp.buf_floats + TH * TW + (size_t)((nk + 3) & ~3)) + 16;
+    if (smem > 200 * 1024) return FT_OK;
+    CUtensorMap in_map, out_map;
+    if (!f32_plane_map(&in_map, p.in, p.Nc, p.Nr, in_planes, BW, cp.SH)) return FT_OK;
+    cp.store_tma = (p.vec_out && f32_plane_map(&out_map, p.out, p.Mc, p.Mr, planes, TW, TH)) ? 1 : 0;
+    if (!cp.store_tma) out_map = in_map;            // unused
+    void *st = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&st, g_fastconv_status);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(conv_tma_kernel<NTAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)   // as much shared memory as the SM has: more resident CTAs
+        e = cudaFuncSetAttribute(conv_tma_kernel<NTAP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    int per_sm = 0, dev = 0, nsm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<NTAP>, kThreads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    if (per_sm < 1) return FT_OK;
+    cp.status = static_cast<int *>(st);
+    const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)per_sm * nsm);
+    conv_tma_kernel<NTAP><<<(unsigned)grid, kThreads, smem, s>>>(in_map, out_map, cp);
+    *used = true;
+    return ft::check_launch();
+}
+
+// 64-row tiles (kernels up to 9 columns, whose registers allow them) need Kr >= 8 and
+// enough tiles for two CTAs per SM; else 32-row tiles
+template <int NTAP>
+ft_status launch_fma_oy(const ConvParams &p, int64_t planes, cudaStream_t s)
+{
+    bool used = false;
+    const ft_status st = launch_tma<NTAP>(p, planes, s, &used);
+    if (st != FT_OK || used) return st;
+    if constexpr (NTAP <= 9) {
+        if (p.Kr < 8) return launch_fma<NTAP, 4>(p, planes, s);
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t tiles64 = planes * ft::ceil_div(p.Mr, 64) * ft::ceil_div(p.Mc, 128);
+        if (tiles64 >= 2 * (int64_t)(nsm > 0 ? nsm : 1)) return launch_fma<NTAP, 8>(p, planes, s);
+    }
+    return launch_fma<NTAP, 4>(p, planes, s);
+}
+
+// taps per row rounded up to the next odd count (at most one zero tap per row)
+ft_status launch_fma_taps(const ConvParams &p, int64_t planes, cudaStream_t s)
+{
+    switch (p.Kc / 2) {
+    case 0: case 1: case 2: return launch_fma_oy<5>(p, planes, s);
+    case 3: return launch_fma_oy<7>(p, planes, s);
+    case 4: return launch_fma_oy<9>(p, planes, s);
+    case 5: return launch_fma_oy<11>(p, planes, s);
+    case 6: return launch_fma_oy<13>(p, planes, s);
+    case 7: return launch_fma_oy<15>(p, planes, s);
+    default: return launch_fma_oy<17>(p, planes, s);
+    }
 }
 
 template <int OY, int WX>
@@ -469,5 +1044,20 @@ extern "C" ft_status fastconv_nd(const float *input, const int64_t *dims, int nd
     }
     if (p.Mr == 1) return launch_by_pad<1, 8>(p, planes, s);          // rank 1 (one row)
     if (p.Kr * p.Kc <= 16) return launch_by_pad<4, 1>(p, planes, s);  // small, memory-bound
-    return launch_by_pad<8, 1>(p, planes, s);                           // FMA-bound
+    if (p.Kr >= 4 && p.Kc <= 17) return launch_fma_taps(p, planes, s); // FMA-bound
+    return launch_by_pad<8, 1>(p, planes, s);                           // wide or flat kernels
+}
+
+extern "C" ft_status fastconv_check(void *stream)
+{
+    int v = 0;
+    const int zero = 0;
+    cudaError_t e = cudaStreamSynchronize(ft::as_stream(stream));
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&v, g_fastconv_status, sizeof(int));
+    if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_fastconv_status, &zero, sizeof(int));
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    return v ? FT_ERR_TIMEOUT : FT_OK;
 }

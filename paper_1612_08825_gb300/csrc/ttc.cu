@@ -409,27 +409,11 @@ extern "C" ft_status ttc_ctx_set_level0_events(ttc_ctx *ctx, void *start, void *
 namespace {
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
-{
-    static std::once_flag once;
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    std::call_once(once, [] {
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-        cudaGetLastError();
-    });
-    return fn;
-}
-
 // 3-D map over npairs frames of H x W uint8 pixels (box: bw columns x TR+1 rows x 1)
 bool u8_frame_map(CUtensorMap *m, const void *base, int W, int H, int npairs, int64_t pitch, int64_t pstride,
                   int bw)
 {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    PFN_cuTensorMapEncodeTiled_v12000 enc = ft::tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)npairs};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pstride};

@@ -14,8 +14,7 @@
 // its copies in flight, and returns.
 #pragma once
 
-#include <cuda.h>
-
+#include "tma.cuh"
 #include "ttc_pass.cuh"
 
 namespace ttc_tma {
@@ -32,7 +31,6 @@ constexpr int FRAME = 2 * BOX + XBOX_PAD;                 // 17792 B, 128-B mult
 constexpr int BUF = 2 * FRAME;                            // both frames
 constexpr unsigned TX = 2u * (2u * BOX + XBOX);           // bytes the copies deliver per tile
 constexpr int SMEM = 2 * BUF + NSUM * NT * 4 + 2 * 8;     // two buffers, reduction, barriers
-constexpr long long WAIT_CYCLES = 4000000000LL;           // about 2 s at 2 GHz
 
 struct TmaParams {
     PassParams p;               // geometry, partials, next level (prev/cur unused)
@@ -40,52 +38,7 @@ struct TmaParams {
     int *status;                // set to 1 when a wait gives up
 };
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait for the phase with the given parity; false when the clock limit passed
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-        : "memory");
-}
+using namespace ft_tma;
 
 // elected thread: copies of tile t of both frames into buffer `buf`
 __device__ __forceinline__ void issue_tile(const TmaParams &tp, const CUtensorMap *ma, const CUtensorMap *mb,

@@ -60,6 +60,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_status_strings_and_version(L):
     assert L.ft_status_string(0) == b"FT_OK"
     assert L.ft_status_string(2) == b"FT_ERR_SHAPE"
+    assert L.ft_status_string(6) == b"FT_ERR_TIMEOUT"
     assert L.ft_status_string(99) == b"FT_ERR_UNKNOWN"
     assert L.ft_version() >= 10000
 

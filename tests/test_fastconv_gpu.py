@@ -26,7 +26,7 @@ def _run(E: np.ndarray, k: np.ndarray, offset: int = 0) -> np.ndarray:
     else:
         x = torch.from_numpy(E).to(dev)
     out = ft.fastconv_nd(x, torch.from_numpy(k).to(dev))
-    torch.cuda.synchronize()
+    ft.fastconv_check()             # no bounded wait gave up
     return out.cpu().numpy()
 
 
@@ -141,3 +141,46 @@ def test_fastconv_full_size_3d_sampled(kk):
     expect = E.astype(np.float64).sum() * k.astype(np.float64).sum()
     scale = np.abs(E).astype(np.float64).sum() * np.abs(k).astype(np.float64).sum()
     assert abs(tot - expect) <= REL * scale
+
+
+@pytest.mark.parametrize("kc", list(range(2, 18)))
+def test_fastconv_fma_kernel_every_width(kc):
+    """The FMA-bound kernel for every kernel width it serves (2..17 columns, 4 or more
+    rows): rows equal to the tile's rows per thread (middle phase of length one) and
+    longer; several 128-column tiles with a ragged tail; a width that is not a
+    multiple of 4 and an offset base (scalar staging); two planes."""
+    for kr in (4, 9):
+        k = scenes.normal_array((kr, kc), seed=100 + kc + kr)
+        _check_full(scenes.uniform_array((45, 600), seed=kc), k)
+        _check_full(scenes.uniform_array((37, 531), seed=kc + 1), k)
+        _check_full(scenes.uniform_array((30, 300), seed=kc + 2), k, offset=1)
+    _check_full(scenes.uniform_array((2, 29, 270), seed=kc + 3), scenes.normal_array((2, 4, kc), seed=kc))
+
+
+def test_fastconv_fma_kernel_large_grid():
+    """Enough tiles for the 64-row variant (16 planes of 300 x 1100; 8 x 7 and 9 x 9
+    kernels), the 32-row variant for wide and tall kernels, compared with the oracle
+    on sampled outputs of every plane."""
+    E = scenes.uniform_array((16, 300, 1100), seed=31)
+    for ks in ((1, 8, 7), (1, 9, 9), (1, 15, 15), (1, 33, 5), (1, 4, 17)):
+        k = scenes.normal_array(ks, seed=sum(ks))
+        got = _run(E, k)
+        rng = np.random.default_rng(ks[1])
+        pts = rng.integers(0, got.size, 4000).astype(np.int64)
+        ref, rabs = oracle.fastconv_points(E, k, pts)
+        g = got.reshape(-1)[pts].astype(np.float64)
+        assert np.all(np.abs(g - ref) <= REL * rabs + 1e-30), ks
+
+
+@pytest.mark.parametrize("shape,kshape", [
+    ((3, 40, 264), (2, 5, 5)), ((3, 40, 264), (3, 7, 9)), ((5, 33, 128), (5, 5, 5)),
+    ((2, 2, 20, 68), (2, 2, 4, 5)), ((2, 3, 17, 36), (3, 1, 6, 7)),
+])
+def test_fastconv_tma_kernel_leading_dims(shape, kshape):
+    """The persistent copy-engine-fed kernel over several leading kernel indices per
+    output tile (planes outside the input skipped), rank 4 (general leading-index
+    decomposition), row lengths that are multiples of 4 (copy engine path) with output
+    rows that are (TMA store) or are not (plain stores) multiples of 4."""
+    E = scenes.uniform_array(shape, seed=sum(shape))
+    k = scenes.normal_array(kshape, seed=sum(kshape))
+    _check_full(E, k)
