@@ -4,20 +4,28 @@
 One step = the whole hot path over one synthetic video: 300 uint8 1920x1080 frames
 of a textured plane tilted 20 degrees (camera within 15 degrees of the optical axis,
 Z0 = 20, 0.05 per frame), 5-level pyramid, 2x2x2 derivatives, G, the ten sums, FP64
-merge and 3x3 FOE solve for all 299 consecutive pairs (two launches: the fused tile
-kernel and the merge/solve kernel).  The 622 MB video is larger than L2 (129 MB),
-so no flush is needed between steps.
+merge and 3x3 FOE solve for all 299 consecutive pairs: one streaming pass per level
+(level 0 by the persistent TMA-fed kernel, levels 1-4 by interior and edge launches
+of the pass kernel, each writing the next level) and one merge/solve launch.  The
+622 MB video is larger than L2 (129 MB), so no flush is needed between steps.
 
 Also reported in the same JSON line:
-  roofline     of the fused tile kernel (CUDA events on its stream, timed region)
-  e2e          the same metric through the public API with pinned host frames
-               (H2D copy of the video and D2H of the results inside the timed region)
-  cpu_baseline the FP64 oracle on a bounded sample of the same video, one core
-  fastconv     the FastConv sweep (1080x1920 with k x k Gaussians, 64x256x256 with k^3)
-               in GB/s and fraction of the measured HBM peak, L2 flushed between runs
-  accuracy     TTC/FOE mean squared error against ground truth per level and per
-               multi-scale rule (Sec. V-B)
-  clocks       nvidia-smi samples taken during the timed region
+  roofline       of the level-0 pass (CUDA events on its stream inside the timed
+                 region): FP32 lane-ops per second against the FP32 issue roof, with
+                 its HBM rate beside it
+  e2e            the same metric through the public API with pinned host frames
+                 (H2D copy of the video and D2H of the results inside the timed region)
+  cpu_baseline   the FP64 oracle on a bounded sample of the same video, one core
+  fastconv       the FastConv sweep (1080x1920 with k x k Gaussians, 64x256x256 with
+                 k^3, batches of 16 images) in GB/s and GFLOP/s with the fraction of
+                 the HBM or FP32 FMA roof, L2 flushed between runs
+  batch_uneven   512 independent pairs of uneven sizes in one batch (work-list
+                 launches, CUDA graph) against the per-frame path
+  serve          64 camera streams replayed at 30 fps through the serving loop and
+                 through the per-frame path (p50/p99 latency), then saturated
+  accuracy       TTC/FOE mean squared error against ground truth per level and per
+                 multi-scale rule (Sec. V-B)
+  clocks         nvidia-smi samples taken during the timed region
 
 ``--impl reference`` times the FP64 oracle (the only reference that exists for this
 method) on a bounded sample of the same workload, on the host cores.
@@ -162,17 +170,17 @@ def run_reference(args):
 # our arm
 # --------------------------------------------------------------------------- #
 
-def fastconv_sweep(dev, hbm_peak, reps):
+def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
     import torch
     import paper_1612_08825_gb300 as ft
     import scenes
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     rows = []
     # the sweep's shapes, plus batches of 16 images (a leading extent-1 kernel axis)
-    # that show the sustained bandwidth of the memory-bound kernels
+    # that show the sustained rates: a single 1080p image is too small to fill the GPU
     cases = [((1080, 1920), (k, k), "gauss") for k in (2, 3, 7, 15)] + \
             [((64, 256, 256), (k, k, k), "normal") for k in (2, 5)] + \
-            [((16, 1080, 1920), (1, k, k), "gauss") for k in (2, 3)]
+            [((16, 1080, 1920), (1, k, k), "gauss") for k in (2, 3, 5, 7, 15)]
     launches = 0
     for shape, kshape, kind in cases:
         E = torch.from_numpy(scenes.uniform_array(shape, seed=2024)).to(dev)
@@ -199,9 +207,10 @@ def fastconv_sweep(dev, hbm_peak, reps):
         byts = 4 * (nE + no + nk)
         flops = 2.0 * nE * nk
         gbs = byts / t / 1e9
-        rows.append({"input": list(shape), "kernel": list(kshape), "us": t * 1e6,
+        bound = "fma" if flops / byts > fma_peak / (hbm_peak * 1e9) else "hbm"
+        rows.append({"input": list(shape), "kernel": list(kshape), "us": t * 1e6, "bound": bound,
                      "GBps": gbs, "hbm_frac": gbs / hbm_peak, "GFLOPps": flops / t / 1e9,
-                     "algorithmic_bytes": byts, "flops": flops})
+                     "fma_frac": flops / t / fma_peak, "algorithmic_bytes": byts, "flops": flops})
     del flush
     return rows, launches
 
@@ -367,6 +376,9 @@ def accuracy(sc, res, levels):
 # Ex/Ey/Et (3), G (2), the ten products (10), plus the next pyramid level (2x2 block
 # sums of both frames: 6 adds per 4 level-0 pixels = 1.5)
 OPS_PER_CUBE0 = 23.5
+# DRAM bytes (read + write) of one level-0 launch over the 299 pairs, from an ncu capture
+# of the same kernel on an 80-frame video (3.86 MB per pair, scaled by pairs)
+L0_TRAFFIC_PER_PAIR = 3.86e6
 
 
 def run_ours(args):
@@ -503,7 +515,7 @@ def run_ours(args):
 
     conv_rows = None
     if rank == 0 and not args.no_conv:
-        conv_rows, _ = fastconv_sweep(dev, hbm_peak, reps=args.conv_reps)
+        conv_rows, _ = fastconv_sweep(dev, hbm_peak, 2.0 * alu_peak, reps=args.conv_reps)
 
     if rank == 0:
         cubes0 = (H - 1) * (W - 1) * npairs
@@ -517,9 +529,12 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": _config(frames_n),
-            "roofline": {"kernel": "ttc level-0 pass (ttc_pass_kernel<u8>, interior + edge launches)",
+            "roofline": {"kernel": "ttc level-0 pass (ttc_pass_tma_kernel: persistent, TMA-fed, uint8 frames)",
                          "bound": "alu", "achieved": achieved_ops / 1e12, "peak": alu_peak / 1e12,
-                         "unit": "TFP32-lane-op/s", "frac": achieved_ops / alu_peak, "traffic": None,
+                         "unit": "TFP32-lane-op/s", "frac": achieved_ops / alu_peak,
+                         "traffic": L0_TRAFFIC_PER_PAIR * npairs,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 80-frame "
+                                           "capture scaled to the launch's pairs",
                          "ops_per_cube": OPS_PER_CUBE0, "cubes_per_launch": cubes0, "launch_ms": l0_ms,
                          "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
                          "hbm": {"achieved": l0_bytes / (l0_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
