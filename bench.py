@@ -133,8 +133,7 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 
 def run_reference(args):
-    import torch
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return 0
     import oracle
@@ -381,6 +380,32 @@ OPS_PER_CUBE0 = 23.5
 L0_TRAFFIC_PER_PAIR = 3.86e6
 
 
+def rank_env():
+    """(world, rank, local rank) from the torch.distributed launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def unit_seed(base: int, rank: int) -> int:
+    """Seed of a rank's own video: ranks process independent units (weak scaling)."""
+    return base + rank
+
+
+def whole_job_rate(elapsed_s: float, units_per_rank: int, device) -> tuple:
+    """Max-over-ranks elapsed time and the whole-job throughput (units of all ranks / that
+    time); the only cross-rank operation besides the barriers."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    world = 1
+    if dist.is_available() and dist.is_initialized():
+        world = dist.get_world_size()
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    return tmax, units_per_rank * world / tmax
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -388,9 +413,7 @@ def run_ours(args):
     import paper_1612_08825_gb300 as ft
     import scenes
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -404,7 +427,7 @@ def run_ours(args):
     frames_n = args.frames
     npairs = frames_n - 1
     # every rank works on its own video (independent pairs: weak scaling)
-    sc = scenes.tilted_plane_scene(H=H, W=W, seed=args.seed + rank)
+    sc = scenes.tilted_plane_scene(H=H, W=W, seed=unit_seed(args.seed, rank))
     frames = scenes.render_sequence(sc, frames_n, device=dev)
     ctx = ft.TtcContext(H, W, LEVELS, npairs, device=dev)
     out = ctx.new_results(npairs * LEVELS)
@@ -444,11 +467,7 @@ def run_ours(args):
     ck = clocks.stop()
     elapsed = start.elapsed_time(end) * 1e-3
     l0_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    t_all = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    tmax = float(t_all.item())
-    value = npairs * args.steps * world / tmax
+    tmax, value = whole_job_rate(elapsed, npairs * args.steps, dev)
 
     res = ft.results_to_numpy(out).reshape(npairs, LEVELS)
 
@@ -496,10 +515,8 @@ def run_ours(args):
             ctx.solve_sequence(host_frames, levels=LEVELS, mode=ft.MODE_FOE, out=hout)
         e1.record(s)
         torch.cuda.synchronize(dev)
-        te = torch.tensor([e0.elapsed_time(e1) * 1e-3], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": npairs * k2 * world / float(te.item()), "unit": UNIT,
+        _, e2e_rate = whole_job_rate(e0.elapsed_time(e1) * 1e-3, npairs * k2, dev)
+        e2e = {"value": e2e_rate, "unit": UNIT,
                "h2d_bytes_per_step": int(host_frames.numel()), "d2h_bytes_per_step": int(hout.numel()),
                "steps": k2}
         e2e_res = ft.results_to_numpy(hout).reshape(npairs, LEVELS)
