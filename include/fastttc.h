@@ -210,6 +210,34 @@ ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_t frame_str
                              ttc_level_result *out, void *stream);
 
 /*
+ * ttc_solve_sequence for a video in host memory, results to host memory (no
+ * counterpart in the paper: the end-to-end path of a camera pipeline).  The pairs are
+ * processed in chunks of FT_SEQ_CHUNK_PAIRS (fewer if the context was created for fewer
+ * pairs): the chunks' frames (one frame shared by consecutive chunks is copied twice) go
+ * to two device buffers of the context on two copy streams of the context, each chunk
+ * is computed on `stream` as soon as its copy has landed, so uploads overlap compute.
+ * Tile plans are those of the whole sequence, and for float frames a chunk after the
+ * first also computes (without reporting) the levels - 1 pairs before it, so that its
+ * frames' pyramids are rounded as in the whole sequence: the records are bitwise those
+ * of ttc_solve_sequence on the same frames (device copies with the same strides),
+ * except for float frames on a context created for at most levels - 1 pairs.
+ *   frames: host, T frames frame_stride_bytes apart (page-locked memory lets the copies
+ *           run asynchronously; pageable memory works but each copy then blocks);
+ *           must stay valid and unchanged until `stream` reaches the end of the call.
+ *   out:    host, (T-1) * levels records (page-locked for an asynchronous copy), valid
+ *           once `stream` has reached the end of the call.
+ * The first call (and a call needing larger buffers) allocates the buffers, the copy
+ * streams and their events in the context (freed by ttc_ctx_destroy); a call that
+ * grows them synchronises the device first.  Calls on one context must be ordered
+ * (one stream).  Errors: as ttc_solve_sequence, FT_ERR_SHAPE (frame stride shorter than
+ * a frame), FT_ERR_CUDA.
+ */
+#define FT_SEQ_CHUNK_PAIRS 64
+ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
+                                  int dtype, int H, int W, int64_t pitch_bytes, int levels, int mode,
+                                  ttc_level_result *out, void *stream);
+
+/*
  * The two stages of ttc_solve_sequence, for callers that time or overlap them.
  * ttc_partial_sums runs the fused pyramid + stencil + G + product + tile-reduction
  * kernel and leaves FP32 per-tile partial sums in the context; ttc_reduce_solve

@@ -105,6 +105,8 @@ def load(path: Optional[str] = None):
     L.ttc_solve_sequence.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _vp, _vp]
     L.ttc_solve_sequence.restype = st
+    L.ttc_solve_sequence_host.argtypes = L.ttc_solve_sequence.argtypes
+    L.ttc_solve_sequence_host.restype = st
     L.ttc_partial_sums.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int64, ctypes.c_int, _vp]
     L.ttc_partial_sums.restype = st
@@ -355,30 +357,36 @@ class TtcContext:
         """T frames -> (T-1) * levels records.
 
         With CUDA frames the records stay on the device (asynchronous).  With host
-        frames (ideally pinned) the frames are copied to the device, solved, and the
-        records are copied back to a host tensor, all on the current stream.
+        frames (ideally pinned) the library uploads them in chunks that overlap the
+        compute and returns the records in a host tensor (ttc_solve_sequence_host), on
+        the current stream; keep `frames` alive until the stream is synchronised.
         """
         L = load()
-        host = not frames.is_cuda
-        if host:
-            if self._staging is None or self._staging.shape != frames.shape or self._staging.dtype != frames.dtype:
-                self._staging = torch.empty(frames.shape, dtype=frames.dtype, device=self.device)
-            self._staging.copy_(frames, non_blocking=True)
-            dev_frames = self._staging
-        else:
-            dev_frames = frames
-        dt, es, T, H, W = self._seq_args(dev_frames)
+        dt, es, T, H, W = self._seq_args(frames)
         n = (T - 1) * levels
-        dev_out = self.new_results(n) if (out is None or host) else out
-        _check(L.ttc_solve_sequence(self._h, dev_frames.data_ptr(), dev_frames.stride(0) * es, T, dt, H, W,
-                                    dev_frames.stride(1) * es, int(levels), int(mode), dev_out.data_ptr(),
-                                    _stream_ptr(dev_frames)), "ttc_solve_sequence")
-        if host:
-            host_out = out if out is not None else torch.empty(n * RESULT_DTYPE.itemsize, dtype=torch.uint8,
-                                                                pin_memory=True)
-            host_out.copy_(dev_out, non_blocking=True)
-            return host_out
-        return dev_out
+        if not frames.is_cuda:
+            if out is None:
+                out = torch.empty(n * RESULT_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+            elif out.is_cuda or out.numel() * out.element_size() < n * RESULT_DTYPE.itemsize:
+                raise ValueError("out must be a host tensor of (T-1) * levels records")
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            _check(L.ttc_solve_sequence_host(self._h, frames.data_ptr(), frames.stride(0) * es, T, dt, H, W,
+                                             frames.stride(1) * es, int(levels), int(mode), out.data_ptr(), stream),
+                   "ttc_solve_sequence_host")
+            self._host_frames = frames          # referenced until the next call
+            return out
+        out = self.new_results(n) if out is None else out
+        _check(L.ttc_solve_sequence(self._h, frames.data_ptr(), frames.stride(0) * es, T, dt, H, W,
+                                    frames.stride(1) * es, int(levels), int(mode), out.data_ptr(),
+                                    _stream_ptr(frames)), "ttc_solve_sequence")
+        return out
+
+    @staticmethod
+    def host_upload_bytes(T: int, frame_bytes: int, max_pairs: int) -> int:
+        """Bytes ttc_solve_sequence_host copies to the device for T frames."""
+        chunk = min(64, max_pairs, T - 1)
+        nchunks = -(-(T - 1) // chunk)
+        return (T - 1 + nchunks) * frame_bytes
 
     def batch_prepare(self, pairs, levels: int = 1):
         """Prepare a batch of independent pairs of any sizes.

@@ -39,6 +39,7 @@ struct SolveParams {
     int64_t ncubes[FT_MAX_LEVELS];
     const int *status;                // nonzero: a stage-1 wait gave up
     ttc_level_result *out;
+    int skip;                         // pairs [0, skip) are not written
 };
 
 __device__ void solve_one(const double s[NSUM], int mode, int level, ttc_level_result *r)
@@ -142,6 +143,7 @@ ttc_solve_kernel(const SolveParams p)
 {
     const int item = blockIdx.x;                 // pair * levels + level
     const int pair = item / p.levels, l = item - pair * p.levels;
+    if (pair < p.skip) return;
     const int ntiles = p.ntiles[l];
     merge_solve(p.partials + p.poff[l] + (int64_t)pair * ntiles * NSUM, ntiles, l, p.inv_scale[l], p.ncubes[l],
                 p.mode, p.status, p.out + item);
@@ -239,7 +241,10 @@ struct Geometry {
 
 // force_tr: 0 picks the tile height per level (16 rows when 64-row tiles would give
 // fewer than ~4 waves of CTAs, so that small levels run as many short CTAs)
-void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geometry &g, int force_tr = 0)
+// plan_pairs: the pair count that decides the tile height per level (0: npairs), so that
+// chunks of a sequence use the tiles of the whole sequence
+void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geometry &g, int force_tr = 0,
+              int plan_pairs = 0)
 {
     g.levels = levels;
     g.npairs = npairs;
@@ -251,7 +256,8 @@ void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geom
         g.tiles_x[l] = (int)ft::ceil_div(g.W[l] - 1, TC);
         int tr = TR;
         if (force_tr) tr = force_tr;
-        else if ((int64_t)npairs * ft::ceil_div(g.H[l] - 1, TR) * g.tiles_x[l] < 1216) tr = ttc_pass::TR_SMALL;
+        else if ((int64_t)(plan_pairs ? plan_pairs : npairs) * ft::ceil_div(g.H[l] - 1, TR) * g.tiles_x[l] < 1216)
+            tr = ttc_pass::TR_SMALL;
         g.tr[l] = tr;
         g.tiles_y[l] = (int)ft::ceil_div(g.H[l] - 1, tr);
         g.ntiles[l] = g.tiles_y[l] * g.tiles_x[l];
@@ -306,6 +312,15 @@ struct ttc_ctx {
     } b;
     int plan_rpw[FT_MAX_LEVELS];      // tile rows per warp per level for batches (0: automatic)
     ttc_pair_desc *h_pairs;           // host copy of the prepared batch (for the autotuner)
+    // sequences in host memory: two device buffers of frame chunks, a results buffer,
+    // copy streams and their events (allocated on first use)
+    unsigned char *ring;
+    size_t ring_bytes;                // per buffer
+    ttc_level_result *ring_out;
+    size_t ring_out_records;
+    cudaStream_t cstream[2];
+    cudaEvent_t ev_start, ev_copied[2], ev_free[2];
+    bool ring_ready;
 };
 
 extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max_levels, int max_pairs)
@@ -390,6 +405,18 @@ extern "C" void ttc_ctx_destroy(ttc_ctx *ctx)
     cudaFree(ctx->d_descs);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+    if (ctx->ring_ready) {
+        cudaStreamSynchronize(ctx->cstream[0]);
+        cudaStreamSynchronize(ctx->cstream[1]);
+        for (int b = 0; b < 2; ++b) {
+            cudaStreamDestroy(ctx->cstream[b]);
+            cudaEventDestroy(ctx->ev_copied[b]);
+            cudaEventDestroy(ctx->ev_free[b]);
+        }
+        cudaEventDestroy(ctx->ev_start);
+    }
+    cudaFree(ctx->ring);
+    cudaFree(ctx->ring_out);
     delete[] ctx->h_pairs;
     delete ctx;
 }
@@ -475,7 +502,8 @@ cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs
 // all levels of npairs pairs: pair p is (prev + p * pair_stride, cur + p * pair_stride);
 // independent = 0 for the consecutive pairs of a video (frame t+1 shared)
 ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64_t pair_stride, int npairs,
-                          int independent, int dtype, int H, int W, int64_t pitch, int levels, cudaStream_t s)
+                          int independent, int dtype, int H, int W, int64_t pitch, int levels, cudaStream_t s,
+                          int plan_pairs = 0)
 {
     if (!ctx || !prev || !cur) return FT_ERR_INVALID_ARG;
     if (npairs < 1) return FT_ERR_SHAPE;
@@ -485,7 +513,7 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
     if (npairs > ctx->max_pairs || levels > ctx->max_levels || H > ctx->max_H || W > ctx->max_W)
         return FT_ERR_WORKSPACE;
     Geometry g;
-    geometry(H, W, levels, dtype, npairs, independent ? 2 * npairs : npairs + 1, g);
+    geometry(H, W, levels, dtype, npairs, independent ? 2 * npairs : npairs + 1, g, 0, plan_pairs);
     if (g.partial_floats > ctx->partial_cap || g.image_bytes > ctx->image_cap) return FT_ERR_WORKSPACE;
     for (int l = 0; l < levels; ++l)
         if ((int64_t)npairs * g.ntiles[l] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
@@ -558,7 +586,7 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
     return FT_OK;
 }
 
-ft_status launch_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream_t s)
+ft_status launch_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream_t s, int skip = 0)
 {
     if (!ctx || !out) return FT_ERR_INVALID_ARG;
     if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
@@ -577,6 +605,7 @@ ft_status launch_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream
     }
     sp.status = ctx->status;
     sp.out = out;
+    sp.skip = skip;
     ttc_solve_kernel<<<(unsigned)(g.npairs * g.levels), 32, 0, s>>>(sp);
     return ft::check_launch();
 }
@@ -1001,6 +1030,119 @@ extern "C" ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_
     ft_status st = ttc_partial_sums(ctx, frames, frame_stride_bytes, T, dtype, H, W, pitch_bytes, levels, stream);
     if (st != FT_OK) return st;
     return launch_solve(ctx, mode, out, ft::as_stream(stream));
+}
+
+namespace {
+
+// the ring, results buffer, copy streams and events of host-frame sequences
+ft_status ring_setup(ttc_ctx *ctx, size_t bytes, size_t records)
+{
+    cudaError_t e = cudaSuccess;
+    if (!ctx->ring_ready) {
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaStreamCreateWithFlags(&ctx->cstream[b], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            ft::set_cuda_error(e);
+            return FT_ERR_CUDA;
+        }
+        ctx->ring_ready = true;
+    }
+    if (bytes > ctx->ring_bytes || records > ctx->ring_out_records) {
+        // the buffers may still be in use by an earlier call
+        e = cudaDeviceSynchronize();
+        if (e == cudaSuccess && bytes > ctx->ring_bytes) {
+            cudaFree(ctx->ring);
+            ctx->ring = nullptr;
+            ctx->ring_bytes = 0;
+            e = cudaMalloc(&ctx->ring, 2 * bytes);
+            if (e == cudaSuccess) ctx->ring_bytes = bytes;
+        }
+        if (e == cudaSuccess && records > ctx->ring_out_records) {
+            cudaFree(ctx->ring_out);
+            ctx->ring_out = nullptr;
+            ctx->ring_out_records = 0;
+            e = cudaMalloc(&ctx->ring_out, records * sizeof(ttc_level_result));
+            if (e == cudaSuccess) ctx->ring_out_records = records;
+        }
+        if (e != cudaSuccess) {
+            ft::set_cuda_error(e);
+            return FT_ERR_CUDA;
+        }
+    }
+    return FT_OK;
+}
+
+}  // namespace
+
+extern "C" ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
+                                             int dtype, int H, int W, int64_t pitch_bytes, int levels, int mode,
+                                             ttc_level_result *out, void *stream)
+{
+    if (!ctx || !frames || !out) return FT_ERR_INVALID_ARG;
+    if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
+    if (T < 2) return FT_ERR_SHAPE;
+    ft_status st = check_frames(dtype, H, W, pitch_bytes);
+    if (st != FT_OK) return st;
+    if ((st = check_levels(H, W, levels)) != FT_OK) return st;
+    if (frame_stride_bytes < pitch_bytes * (H - 1) + (int64_t)W * elem_size(dtype)) return FT_ERR_SHAPE;
+    if (H > ctx->max_H || W > ctx->max_W || levels > ctx->max_levels) return FT_ERR_WORKSPACE;
+    const int npairs = T - 1;
+    // Float frames: a frame's pyramid images are rounded differently when written as
+    // the first frame of a pair (block sums of its pixels) and as the second (first
+    // frame's sums plus the sums of the differences), and the level-l image of a second
+    // frame depends on the level-(l-1) image of the frame before it.  So that every
+    // record equals the whole-sequence call, a chunk after the first also computes the
+    // levels - 1 pairs before it (their records are not written).  uint8 sums are exact
+    // either way.
+    const int lead = (dtype == FT_F32 && ctx->max_pairs > levels - 1) ? levels - 1 : 0;
+    const int chunk = std::min(std::min(FT_SEQ_CHUNK_PAIRS, ctx->max_pairs - lead), npairs);
+    const int nchunks = (npairs + chunk - 1) / chunk;
+    const size_t frame_bytes = (size_t)(pitch_bytes * (H - 1) + (int64_t)W * elem_size(dtype));
+    const size_t buf_bytes =
+        ((size_t)(chunk + lead) * (size_t)frame_stride_bytes + frame_bytes + 255) / 256 * 256;
+    if ((st = ring_setup(ctx, buf_bytes, (size_t)npairs * levels)) != FT_OK) return st;
+    cudaStream_t s = ft::as_stream(stream);
+    const unsigned char *host = static_cast<const unsigned char *>(frames);
+    cudaError_t e = cudaEventRecord(ctx->ev_start, s);
+    int launches = 0;
+    for (int k = 0; k < nchunks && e == cudaSuccess; ++k) {
+        const int b = k & 1;
+        const int p0 = k * chunk, n = std::min(chunk, npairs - p0);
+        const int x = k > 0 ? std::min(lead, p0) : 0;   // extra pairs before the chunk
+        const int f0 = p0 - x;                   // the chunk's first frame
+        unsigned char *dev = ctx->ring + (size_t)b * ctx->ring_bytes;
+        cudaStream_t cs = ctx->cstream[b];
+        // the buffer is free once the chunk two back has been computed (or, for the
+        // first two chunks, once the stream has reached this call)
+        e = cudaStreamWaitEvent(cs, k < 2 ? ctx->ev_start : ctx->ev_free[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dev, host + (size_t)f0 * frame_stride_bytes,
+                                (size_t)(n + x) * frame_stride_bytes + frame_bytes, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied[b], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_copied[b], 0);
+        if (e != cudaSuccess) break;
+        st = launch_partials(ctx, dev, dev + frame_stride_bytes, frame_stride_bytes, n + x, 0, dtype, H, W,
+                             pitch_bytes, levels, s, npairs);
+        if (st != FT_OK) return st;
+        launches += ctx->launches + 1;
+        e = cudaEventRecord(ctx->ev_free[b], s);
+        if (e != cudaSuccess) break;
+        st = launch_solve(ctx, mode, ctx->ring_out + (size_t)f0 * levels, s, x);
+        if (st != FT_OK) return st;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, ctx->ring_out, (size_t)npairs * levels * sizeof(ttc_level_result),
+                            cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    ctx->launches = launches;
+    return FT_OK;
 }
 
 extern "C" ft_status ttc_derivatives(const void *prev, const void *cur, int dtype, int H, int W,

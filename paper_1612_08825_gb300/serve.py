@@ -338,13 +338,18 @@ class PerFrameEngine:
     ``ttc_solve`` call against the stream's resident previous frame (pyramids are
     rebuilt in the context each time), one pair after another."""
 
-    def __init__(self, max_H: int, max_W: int, levels: int, dtype=torch.uint8, mode: int = MODE_FOE, device=None):
+    def __init__(self, max_H: int, max_W: int, levels: int, dtype=torch.uint8, mode: int = MODE_FOE, device=None,
+                 max_items: int = 64):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.levels, self.dtype, self.mode = levels, dtype, mode
         self.max_H, self.max_W = max_H, max_W
         self.ctx = TtcContext(max_H, max_W, max_levels=levels, max_pairs=1, device=self.device)
         self.compute = torch.cuda.Stream(self.device)
         self.dev_out = self.ctx.new_results(levels)
+        # pinned host records, a ring as deep as a tick can be (two ticks in flight)
+        self.host_ring = torch.empty((2 * max_items, levels * RESULT_DTYPE.itemsize), dtype=torch.uint8,
+                                     pin_memory=True)
+        self.ring_pos = 0
         self.launches = 0
 
     def fixed_bytes(self) -> int:
@@ -379,7 +384,8 @@ class PerFrameEngine:
                 if h.cur >= 0:
                     self.ctx.solve(h.frames[h.cur], h.frames[slot], self.levels, self.mode, out=self.dev_out)
                     self.launches += self.ctx.last_launch_count
-                    host = torch.empty(self.dev_out.numel(), dtype=torch.uint8, pin_memory=True)
+                    host = self.host_ring[self.ring_pos % self.host_ring.shape[0]]
+                    self.ring_pos += 1
                     host.copy_(self.dev_out, non_blocking=True)
                     recs.append(host)
                 else:
@@ -396,7 +402,7 @@ class PerFrameEngine:
         ticket[0].synchronize()
 
     def results(self, ticket):
-        return [results_to_numpy(r) if r is not None else None for r in ticket[1]]
+        return [results_to_numpy(r).copy() if r is not None else None for r in ticket[1]]
 
 
 def latency_summary(done: List[Completed]) -> dict:

@@ -110,6 +110,55 @@ def test_sequence_equals_single_pairs_bitwise():
     ctx.close()
 
 
+@pytest.mark.parametrize("T,H,W,dtype,pinned,max_pairs", [
+    (150, 1080, 1920, torch.uint8, True, 149),      # three chunks (64, 64, 21), TMA level 0
+    (40, 243, 337, torch.uint8, False, 39),         # one chunk, pageable frames, odd sizes
+    (70, 96, 160, torch.float32, True, 20),         # chunks limited by the context (20, 20, 20, 9)
+])
+def test_host_sequence_equals_device_sequence_bitwise(T, H, W, dtype, pinned, max_pairs):
+    """Host frames in chunks whose uploads overlap the compute give bitwise the records
+    of the device-frame call (tile plans of the whole sequence)."""
+    sc = scenes.tilted_plane_scene(H=H, W=W, seed=T, m=16, quantize=dtype == torch.uint8)
+    fr = scenes.render_sequence(sc, T, device=DEV)
+    ctx = ft.TtcContext(H, W, 4, max_pairs)
+    if max_pairs >= T - 1:
+        dev = ft.results_to_numpy(ctx.solve_sequence(fr, levels=4, mode=1)).reshape(T - 1, 4)
+    else:
+        # the device reference in pieces of the context's size, tile plan of the whole sequence
+        big = ft.TtcContext(H, W, 4, T - 1)
+        dev = ft.results_to_numpy(big.solve_sequence(fr, levels=4, mode=1)).reshape(T - 1, 4)
+        big.close()
+    host = fr.cpu()
+    if pinned:
+        host = host.pin_memory()
+    got = ctx.solve_sequence(host, levels=4, mode=1)
+    torch.cuda.synchronize()
+    assert not got.is_cuda
+    got = ft.results_to_numpy(got).reshape(T - 1, 4)
+    assert got.tobytes() == dev.tobytes()
+    again = ft.results_to_numpy(ctx.solve_sequence(host, levels=4, mode=1)).reshape(T - 1, 4)
+    torch.cuda.synchronize()
+    assert again.tobytes() == dev.tobytes()
+    ctx.close()
+
+
+def test_host_sequence_errors():
+    ctx = ft.TtcContext(64, 64, 2, 4)
+    fr = torch.zeros((3, 64, 64), dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        ctx.solve_sequence(fr, levels=2, out=torch.empty(10, dtype=torch.uint8))
+    L = ft.load()
+    import ctypes
+    out = torch.empty(2 * 2 * ft.RESULT_DTYPE.itemsize, dtype=torch.uint8)
+    # frame stride shorter than a frame
+    assert L.ttc_solve_sequence_host(ctx._h, fr.data_ptr(), 64 * 32, 3, 0, 64, 64, 64, 2, 1, out.data_ptr(),
+                                     None) == 2
+    assert L.ttc_solve_sequence_host(ctx._h, fr.data_ptr(), 64 * 64, 1, 0, 64, 64, 64, 2, 1, out.data_ptr(),
+                                     None) == 2
+    assert L.ttc_solve_sequence_host(ctx._h, None, 64 * 64, 3, 0, 64, 64, 64, 2, 1, out.data_ptr(), None) == 1
+    ctx.close()
+
+
 def test_two_stage_api_equals_one_call():
     sc = scenes.tilted_plane_scene(H=100, W=150, seed=13, m=16)
     fr = scenes.render_sequence(sc, 3).to(DEV)
