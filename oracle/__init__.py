@@ -65,6 +65,7 @@ def _load():
             lib.oracle_conv_out_dims.argtypes = [ctypes.c_int, _i64p, _i64p, _i64p]
             lib.oracle_downsample.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, _f64p]
             lib.oracle_derivatives.argtypes = [_f64p, _f64p, ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p]
+            lib.oracle_gradient.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, _f64p, _f64p]
             lib.oracle_sums.argtypes = [_f64p, _f64p, _f64p, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, _f64p, _f64p]
             lib.oracle_solve.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
@@ -132,6 +133,17 @@ def downsample(img):
     out = np.empty((H // 2, W // 2), dtype=np.float64)
     _load().oracle_downsample(_p(img), H, W, _p(out))
     return out
+
+
+def gradient(E):
+    """Gradient magnitude and direction of one image (Sec. II, Eq. Emag, Eq. Eangle),
+    each (H-1) x (W-1)."""
+    E = _f64(E)
+    H, W = E.shape
+    mag = np.empty((H - 1, W - 1), dtype=np.float64)
+    ang = np.empty((H - 1, W - 1), dtype=np.float64)
+    _load().oracle_gradient(_p(E), H, W, _p(mag), _p(ang))
+    return mag, ang
 
 
 def derivatives(E0, E1):

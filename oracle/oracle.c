@@ -9,7 +9,7 @@
  * Paper: "Accelerated Convolutions for Efficient Multi-Scale Time to Contact
  * Computation in Julia" (Amini, Horn, Edelman).
  *
- * Readings of the paper that this file fixes (all listed in the design doc):
+ * Readings of the paper that this file fixes:
  *  - Eq. conv2 is read as the full linear convolution (kernel flipped, output
  *    extent N + K - 1 per dimension), the operation FastConv replaces in Sec. IV-D.
  *  - The derivative stencils are the 2x2x2 time-averaged first differences whose
@@ -134,6 +134,28 @@ void oracle_downsample(const double *in, int H, int W, double *out)
             double s = in[(int64_t)(2 * i) * W + 2 * j] + in[(int64_t)(2 * i) * W + 2 * j + 1]
                      + in[(int64_t)(2 * i + 1) * W + 2 * j] + in[(int64_t)(2 * i + 1) * W + 2 * j + 1];
             out[(int64_t)i * w + j] = s / 4.0;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. II, Eq. Emag and Eq. Eangle: gradient magnitude and direction         */
+/* ------------------------------------------------------------------------ */
+
+/* Single image E (H x W): at every 2x2 block centre, Ex and Ey from the Sec. II mask
+ * 1/2 [[-1, 1], [-1, 1]] (and its transpose), then |E| = sqrt(Ex^2 + Ey^2) and
+ * theta = four-quadrant inverse tangent of (Ey, Ex), in [-pi, pi].  Outputs
+ * (H-1) x (W-1); either may be NULL. */
+void oracle_gradient(const double *E, int H, int W, double *mag, double *dir)
+{
+    int w = W - 1;
+    for (int i = 0; i < H - 1; ++i)
+        for (int j = 0; j < W - 1; ++j) {
+            const double a = E[(int64_t)i * W + j], b = E[(int64_t)i * W + j + 1];
+            const double c = E[(int64_t)(i + 1) * W + j], d = E[(int64_t)(i + 1) * W + j + 1];
+            const double ex = 0.5 * ((b - a) + (d - c));
+            const double ey = 0.5 * ((c - a) + (d - b));
+            if (mag) mag[(int64_t)i * w + j] = sqrt(ex * ex + ey * ey);
+            if (dir) dir[(int64_t)i * w + j] = atan2(ey, ex);
         }
 }
 

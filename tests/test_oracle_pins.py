@@ -145,6 +145,36 @@ def test_derivatives_golden_paper_mask():
     np.testing.assert_allclose(Ey, scipy.signal.correlate2d(E, np.array(g["mask_y"]), "valid"), atol=1e-14)
 
 
+def test_gradient_golden_edges():
+    for case in _golden("gradient_edges_sec2.json")["cases"]:
+        mag, ang = oracle.gradient(np.array(case["image"], float))
+        np.testing.assert_array_equal(mag, np.array(case["mag"], float), err_msg=case["name"])
+        np.testing.assert_allclose(ang, np.pi * np.array(case["dir_over_pi"], float), atol=1e-15,
+                                   err_msg=case["name"])
+
+
+@pytest.mark.parametrize("a,b", [(1.5, 0.0), (0.0, 2.0), (-1.0, 0.5), (-0.75, -2.0), (3.0, -1.0)])
+def test_gradient_closed_form_on_planes(a, b):
+    """E = a x + b y (x: column, y: row) has Ex = a, Ey = b on every block: the magnitude
+    is hypot(a, b) and the direction atan2(b, a), one value per quadrant."""
+    yy, xx = np.mgrid[0:7, 0:9].astype(float)
+    mag, ang = oracle.gradient(a * xx + b * yy + 5.0)
+    np.testing.assert_allclose(mag, np.hypot(a, b), rtol=1e-14)
+    np.testing.assert_allclose(ang, np.arctan2(b, a), atol=1e-14)
+
+
+def test_gradient_transpose_and_range():
+    """Transposing the image swaps Ex and Ey: the magnitude is transposed and the
+    direction reflects about pi/4; every direction lies in [-pi, pi]."""
+    E = np.random.default_rng(17).standard_normal((9, 12))
+    mag, ang = oracle.gradient(E)
+    magT, angT = oracle.gradient(E.T)
+    np.testing.assert_allclose(magT, mag.T, rtol=1e-14)
+    np.testing.assert_allclose(np.cos(angT), np.sin(ang).T, atol=1e-12)
+    np.testing.assert_allclose(np.sin(angT), np.cos(ang).T, atol=1e-12)
+    assert np.all(np.abs(ang) <= np.pi)
+
+
 def test_derivatives_equal_interior_of_3d_full_conv():
     rng = np.random.default_rng(7)
     E0 = rng.standard_normal((5, 6))
