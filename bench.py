@@ -18,7 +18,9 @@ Also reported in the same JSON line:
   cpu_baseline   the FP64 oracle on a bounded sample of the same video, one core
   fastconv       the FastConv sweep (1080x1920 with k x k Gaussians, 64x256x256 with
                  k^3, batches of 16 images) in GB/s and GFLOP/s with the fraction of
-                 the HBM or FP32 FMA roof, L2 flushed between runs
+                 the HBM or FP32 FMA roof, L2 flushed between runs; separable Gaussians
+                 through one 1-D pass per axis against the direct path
+  gradient       gradient magnitude and direction of 1080p uint8 images, GB/s
   batch_uneven   512 independent pairs of uneven sizes in one batch (work-list
                  launches, CUDA graph) against the per-frame path
   serve          64 camera streams replayed at 30 fps through the serving loop and
@@ -210,8 +212,83 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
         rows.append({"input": list(shape), "kernel": list(kshape), "us": t * 1e6, "bound": bound,
                      "GBps": gbs, "hbm_frac": gbs / hbm_peak, "GFLOPps": flops / t / 1e9,
                      "fma_frac": flops / t / fma_peak, "algorithmic_bytes": byts, "flops": flops})
+    # separable kernels through one 1-D pass per axis (normalised Gaussians): time and
+    # the speedup over the direct path for the same output
+    def timed(fn):
+        ts = []
+        for i in range(reps + 2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            ts.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        return float(np.median([a.elapsed_time(b) for a, b in ts[2:]])) * 1e-3
+
+    for shape, ksz in (((1080, 1920), 15), ((16, 1080, 1920), 15), ((64, 256, 256), 5)):
+        E = torch.from_numpy(scenes.uniform_array(shape, seed=2024)).to(dev)
+        g = scenes.gaussian_kernel(ksz, ndim=1)
+        nsep = 2 if len(shape) == 3 and shape[0] == 16 else len(shape)
+        ks = [1] * (len(shape) - nsep) + [ksz] * nsep
+        facs = [torch.ones(1, device=dev)] * (len(shape) - nsep) + [torch.from_numpy(g).to(dev)] * nsep
+        full = facs[0].cpu().numpy().astype(np.float64)
+        for f in facs[1:]:
+            full = np.multiply.outer(full, f.cpu().numpy().astype(np.float64))
+        kfull = torch.from_numpy(full.astype(np.float32)).to(dev)
+        out = ft.fastconv_nd(E, kfull)
+        scratch = torch.empty_like(out)
+        t_sep = timed(lambda: ft.fastconv_separable(E, facs, out=out, scratch=scratch))
+        t_dir = timed(lambda: ft.fastconv_nd(E, kfull, out=out))
+        launches += 2 * (reps + 2) * (1 + len(shape))
+        flops = 2.0 * E.numel() * kfull.numel()
+        cur, byts = list(shape), 0
+        for d, k in enumerate(ks):          # every pass reads its input and writes its output
+            nxt = list(cur)
+            nxt[d] += k - 1
+            byts += 4 * (int(np.prod(cur)) + int(np.prod(nxt)))
+            cur = nxt
+        rows.append({"input": list(shape), "kernel": ks, "path": "separable", "us": t_sep * 1e6,
+                     "bound": "hbm", "GBps": byts / t_sep / 1e9, "hbm_frac": byts / t_sep / 1e9 / hbm_peak,
+                     "algorithmic_bytes": byts, "direct_us": t_dir * 1e6, "speedup_vs_direct": t_dir / t_sep,
+                     "direct_equivalent_GFLOPps": flops / t_sep / 1e9})
     del flush
     return rows, launches
+
+
+def gradient_bench(dev, hbm_peak, reps):
+    """Gradient magnitude and direction (Sec. II) of one 1080p uint8 image and of 16
+    images: bytes = pixels read once + two float outputs written."""
+    import torch
+    import paper_1612_08825_gb300 as ft
+    import scenes
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    sc = scenes.tilted_plane_scene(H=H, W=W, seed=5)
+    img = scenes.render(sc, 0.0, device=dev)
+    s = torch.cuda.current_stream(dev)
+    for n in (1, 16):
+        imgs = [img.clone() for _ in range(n)]
+        outs = [(torch.empty((H - 1, W - 1), device=dev), torch.empty((H - 1, W - 1), device=dev)) for _ in range(n)]
+        L = ft.load()
+        ts = []
+        for i in range(reps + 2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for im, (m, a) in zip(imgs, outs):
+                L.ttc_gradient(im.data_ptr(), 0, H, W, W, m.data_ptr(), a.data_ptr(), s.cuda_stream)
+            e1.record(s)
+            ts.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        t = float(np.median([a.elapsed_time(b) for a, b in ts[2:]])) * 1e-3
+        byts = n * (H * W + 8 * (H - 1) * (W - 1))
+        rows.append({"images": n, "H": H, "W": W, "dtype": "u8", "us": t * 1e6, "GBps": byts / t / 1e9,
+                     "hbm_frac": byts / t / 1e9 / hbm_peak, "algorithmic_bytes": byts})
+    del flush
+    return rows
 
 
 def batch_bench(dev, args):
@@ -532,8 +609,10 @@ def run_ours(args):
         serve = serve_bench(dev, args)
 
     conv_rows = None
+    grad_rows = None
     if rank == 0 and not args.no_conv:
         conv_rows, _ = fastconv_sweep(dev, hbm_peak, 2.0 * alu_peak, reps=args.conv_reps)
+        grad_rows = gradient_bench(dev, hbm_peak, reps=args.conv_reps)
 
     if rank == 0:
         cubes0 = (H - 1) * (W - 1) * npairs
@@ -567,6 +646,7 @@ def run_ours(args):
             "parity": parity,
             "accuracy": accuracy(sc, res, LEVELS),
             "fastconv": conv_rows,
+            "gradient": grad_rows,
             "batch_uneven": batch,
             "serve": serve,
         }

@@ -83,6 +83,34 @@ ft_status fastconv_nd(const float *input, const int64_t *dims, int nd,
                       const float *kernel, const int64_t *kdims, float *out, void *stream);
 
 /*
+ * Full n-D convolution with a separable kernel k = f_0 (x) f_1 (x) ... (x) f_{nd-1}
+ * (outer product of one vector per axis; the paper's Future Work: directional
+ * derivatives, Gaussians and block averages are separable): one 1-D full convolution
+ * per axis, in axis order, so an output costs sum(kdims) multiply-adds instead of
+ * prod(kdims).  Same result as fastconv_nd with the outer-product kernel, up to the
+ * order of the FP32 sums.
+ *   factors: host array of nd device pointers; factors[d] holds kdims[d] floats.
+ *   scratch: device, prod(dims + kdims - 1) floats (may be NULL when nd == 1); the
+ *            passes alternate between scratch and out so that the last one writes out.
+ *   input, out, scratch must not overlap.  Other arguments as fastconv_nd.
+ * Errors: as fastconv_nd; FT_ERR_INVALID_ARG (a null factor, missing scratch, aliased
+ * buffers).
+ */
+ft_status fastconv_separable(const float *input, const int64_t *dims, int nd, const float *const *factors,
+                             const int64_t *kdims, float *out, float *scratch, void *stream);
+
+/*
+ * Host only: tests whether a kernel (host, prod(kdims) floats, row-major) is the outer
+ * product of one vector per axis, within rel_tol * max|k| at every entry.  On success
+ * writes the factors to `factors` (host, sum(kdims) floats: factor 0, then factor 1,
+ * ...) and returns 1; returns 0 when the kernel is not separable, -1 on invalid
+ * arguments (null pointers, nd outside [1, FT_MAX_NDIM], an extent < 1, more than 2^26
+ * entries, rel_tol < 0).  The factors are the kernel's fibres through its largest
+ * entry, the first one scaled so that their product reproduces the kernel.
+ */
+int fastconv_factor(const float *kernel, const int64_t *kdims, int nd, double rel_tol, float *factors);
+
+/*
  * Synchronises `stream`, then reports (and clears) the device-wide FastConv status
  * word of the current device: FT_ERR_TIMEOUT if a bounded wait of a FastConv kernel
  * gave up since the last check (its output is incomplete), FT_OK otherwise.  No
@@ -199,6 +227,20 @@ ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, int dtype, 
 #define FT_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dtype, int H, int W, int64_t pitch_bytes,
                             int levels, int mode, ttc_level_result *out, void *stream);
+
+/*
+ * Gradient magnitude and direction of one image (Sec. II, Eq. Emag and Eq. Eangle): at
+ * every 2x2 block centre, Ex = 1/2 [(E(x+1,y) - E(x,y)) + (E(x+1,y+1) - E(x,y+1))] and
+ * Ey likewise down the rows (the Sec. II mask and its transpose; x: column, y: row),
+ *     mag = sqrt(Ex^2 + Ey^2),  dir = atan2(Ey, Ex) in [-pi, pi]  (FP32).
+ *   image : device, H rows of W pixels (FT_U8 or FT_F32), row stride pitch_bytes.
+ *   mag, dir : device, (H-1) x (W-1) floats each, row-major contiguous; either may be
+ *              NULL (not both).
+ * Errors: FT_ERR_INVALID_ARG (null image, both outputs null, bad dtype), FT_ERR_SHAPE
+ * (H or W < 2, pitch), FT_ERR_UNSUPPORTED (more than 524280 rows), FT_ERR_CUDA.
+ */
+ft_status ttc_gradient(const void *image, int dtype, int H, int W, int64_t pitch_bytes, float *mag, float *dir,
+                       void *stream);
 
 /*
  * The same for the T-1 consecutive pairs (t, t+1) of a video of T frames stored

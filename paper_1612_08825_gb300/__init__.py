@@ -20,7 +20,8 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "fastconv_check", "ttc_derivatives",
+    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "fastconv_check", "fastconv_separable",
+    "factor_kernel", "ttc_derivatives", "gradient",
     "ttc_solve_noalloc",
     "TtcContext", "RESULT_DTYPE", "results_to_numpy", "select_level",
     "MODE_TTC", "MODE_FOE", "FLAG_SINGULAR", "FLAG_C_ZERO", "FLAG_RECEDING", "MAX_LEVELS",
@@ -87,9 +88,16 @@ def load(path: Optional[str] = None):
     L.fastconv_nd.restype = st
     L.fastconv_check.argtypes = [_vp]
     L.fastconv_check.restype = st
+    L.fastconv_separable.argtypes = [_vp, _i64p, ctypes.c_int, ctypes.POINTER(_vp), _i64p, _vp, _vp, _vp]
+    L.fastconv_separable.restype = st
+    L.fastconv_factor.argtypes = [ctypes.POINTER(ctypes.c_float), _i64p, ctypes.c_int, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_float)]
+    L.fastconv_factor.restype = ctypes.c_int
     L.ttc_derivatives.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                   _vp, _vp, _vp, _vp, _vp]
     L.ttc_derivatives.restype = st
+    L.ttc_gradient.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp]
+    L.ttc_gradient.restype = st
     L.ttc_ctx_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.ttc_ctx_create.restype = st
     L.ttc_ctx_destroy.argtypes = [_vp]
@@ -191,6 +199,48 @@ def fastconv_nd(x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = 
     return out
 
 
+def fastconv_separable(x: torch.Tensor, factors, out: Optional[torch.Tensor] = None,
+                       scratch: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Full convolution of x with the outer product of the 1-D factors (one per axis)."""
+    L = load()
+    _require_cuda(x, "x")
+    if x.dtype != torch.float32 or len(factors) != x.dim():
+        raise ValueError("float32 input and one factor per axis")
+    fs = []
+    for f in factors:
+        _require_cuda(f, "factor")
+        if f.dtype != torch.float32 or f.dim() != 1:
+            raise ValueError("factors are 1-D float32 tensors")
+        fs.append(f.contiguous())
+    x = x.contiguous()
+    kdims = [f.numel() for f in fs]
+    od = fastconv_out_dims(x.shape, kdims)
+    if out is None:
+        out = torch.empty(od, dtype=torch.float32, device=x.device)
+    if scratch is None and x.dim() >= 2:
+        scratch = torch.empty(od, dtype=torch.float32, device=x.device)
+    ptrs = (_vp * len(fs))(*[f.data_ptr() for f in fs])
+    _check(L.fastconv_separable(x.data_ptr(), _dims(x.shape), x.dim(), ptrs, _dims(kdims), out.data_ptr(),
+                                scratch.data_ptr() if scratch is not None else None, _stream_ptr(x)),
+           "fastconv_separable")
+    return out
+
+
+def factor_kernel(k, rel_tol: float = 1e-6):
+    """Host rank-1 test: the per-axis factors of a separable kernel, or None."""
+    L = load()
+    k = np.ascontiguousarray(np.asarray(k.cpu() if isinstance(k, torch.Tensor) else k, dtype=np.float32))
+    kd = list(k.shape)
+    f = np.empty(sum(kd), dtype=np.float32)
+    r = L.fastconv_factor(k.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _dims(kd), k.ndim, float(rel_tol),
+                          f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    if r < 0:
+        raise ValueError("invalid kernel for fastconv_factor")
+    if r == 0:
+        return None
+    return list(np.split(f, np.cumsum(kd)[:-1]))
+
+
 def fastconv_check(device=None):
     """Synchronise the current stream; raise FtError if a FastConv wait gave up since the last check."""
     L = load()
@@ -228,6 +278,25 @@ def ttc_derivatives(prev: torch.Tensor, cur: torch.Tensor, with_G: bool = True):
                              outs[0].data_ptr(), outs[1].data_ptr(), outs[2].data_ptr(), G,
                              _stream_ptr(prev)), "ttc_derivatives")
     return tuple(outs)
+
+
+def gradient(image: torch.Tensor, with_mag: bool = True, with_dir: bool = True):
+    """Gradient magnitude and direction of one image (Sec. II, Eq. Emag, Eq. Eangle):
+    two (H-1) x (W-1) float32 tensors (None for an output not asked for)."""
+    L = load()
+    _require_cuda(image, "image")
+    if image.dim() != 2 or image.stride(1) != 1:
+        raise ValueError("image must be 2-D with contiguous rows")
+    if not (with_mag or with_dir):
+        raise ValueError("ask for at least one output")
+    dt, es = _frame_args(image)
+    H, W = image.shape
+    mag = torch.empty((H - 1, W - 1), dtype=torch.float32, device=image.device) if with_mag else None
+    ang = torch.empty((H - 1, W - 1), dtype=torch.float32, device=image.device) if with_dir else None
+    _check(L.ttc_gradient(image.data_ptr(), dt, H, W, image.stride(0) * es,
+                          mag.data_ptr() if mag is not None else None, ang.data_ptr() if ang is not None else None,
+                          _stream_ptr(image)), "ttc_gradient")
+    return mag, ang
 
 
 def results_to_numpy(t: torch.Tensor) -> np.ndarray:

@@ -15,36 +15,20 @@
 // memory so that global stores are fully coalesced 128-byte rows whatever the
 // alignment of the output row length.  Accumulation is FP32 FMA in a fixed order.
 //
-// FMA-bound plane kernels (4..129 rows, up to 17 columns) use conv_fma_kernel instead:
+// Kernels of up to 17 columns use the persistent TMA-fed kernel of fastconv_tma.cu
+// when the input rows meet the copy engine's rules, else (4..129 rows) conv_fma_kernel:
 // asynchronous zero-filling copies for the staging and a branch-free schedule of the
 // multiply-adds.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <vector>
 
-#include "common.cuh"
-#include "tma.cuh"
-
-// set to 1 when a wait of a TMA-fed FastConv kernel gave up (read by fastconv_check)
-__device__ int g_fastconv_status;
+#include "conv.cuh"
 
 namespace {
 
-constexpr int kThreads = 256;
-
-struct ConvParams {
-    const float *in;
-    const float *ker;
-    float *out;
-    int nlead;                           // number of leading dimensions (rank - 2, or 0)
-    int64_t in_lead[FT_MAX_NDIM];        // leading input extents
-    int64_t k_lead[FT_MAX_NDIM];         // leading kernel extents
-    int64_t out_lead[FT_MAX_NDIM];       // leading output extents
-    int64_t k_lead_total;                // prod(k_lead)
-    int64_t Nr, Nc, Kr, Kc, Mr, Mc;      // plane extents: input, kernel, output
-    int64_t tiles_x, tiles_per_plane;
-    int vec_in;                          // 1: input rows allow 16-byte loads
-    int vec_out;                         // 1: output rows allow 16-byte stores
-};
+using namespace ft_conv;
 
 // TW = 128 * WX columns, TH = OY * (8 / WX) rows; PADC >= Kc - 1, multiple of 4.
 template <int PADC, int OY, int WX>
@@ -205,40 +189,6 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// the NTAP taps of one kernel row (float4 groups in shared memory) applied to one
-// output row's four columns from the thread's window: acc[c] += k[b] * in[c - b]
-template <int NTAP, int PADC>
-__device__ __forceinline__ void fma_row(float (&acc)[4], const float (&win)[PADC + 4], const float4 *krow)
-{
-#pragma unroll
-    for (int g = 0; g < (NTAP + 3) / 4; ++g) {
-        const float4 k4 = krow[g];
-        const float kv[4] = {k4.x, k4.y, k4.z, k4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int b = 4 * g + j;
-            if (b < NTAP) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[c] = fmaf(kv[j], win[c - b + PADC], acc[c]);
-            }
-        }
-    }
-}
-
-template <int PADC>
-__device__ __forceinline__ void load_window(float (&win)[PADC + 4], const float *row)
-{
-    const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-    for (int v = 0; v < (PADC + 4) / 4; ++v) {
-        const float4 f = r4[v];
-        win[4 * v + 0] = f.x;
-        win[4 * v + 1] = f.y;
-        win[4 * v + 2] = f.z;
-        win[4 * v + 3] = f.w;
-    }
-}
 
 // A CTA owns TH = 8 * OY output rows x 128 columns; thread (warp w, lane l) computes
 // rows OY * w .. + OY - 1 and columns 4l .. 4l + 3.  The zero-padded input tile
@@ -632,312 +582,11 @@ ft_status launch_fma(const ConvParams &p0, int64_t planes, cudaStream_t s)
     return ft::check_launch();
 }
 
-// ---------------------------------------------------------------------------
-// persistent FMA-bound kernel fed by the Tensor Memory Accelerator
-// ---------------------------------------------------------------------------
-
-// input plane feeding output plane `plane` through leading kernel index R, or -1 when
-// it lies outside the input (ranks <= 3 need no division)
-__device__ __forceinline__ int64_t lead_plane(const ConvParams &p, int64_t plane, int64_t R)
-{
-    if (p.nlead == 0) return 0;
-    if (p.nlead == 1) {
-        const int64_t q = plane - R;
-        return (q >= 0 && q < p.in_lead[0]) ? q : -1;
-    }
-    int64_t q = 0, stride = 1, rp = plane, rr = R;
-    for (int d = p.nlead - 1; d >= 0; --d) {
-        const int64_t pd = rp % p.out_lead[d], rd = rr % p.k_lead[d];
-        rp /= p.out_lead[d];
-        rr /= p.k_lead[d];
-        const int64_t qd = pd - rd;
-        if (qd < 0 || qd >= p.in_lead[d]) return -1;
-        q += qd * stride;
-        stride *= p.in_lead[d];
-    }
-    return q;
-}
-
-namespace conv_tma {
-
-constexpr int OY = 4, TH = 8 * OY, TW = 128;
-
-struct Params {
-    ConvParams p;
-    int planes;                  // output planes
-    int tiles_x, tiles_per_plane;
-    int SH;                      // staged rows per tile: TH + Kr - 1
-    int buf_floats;              // floats per staging buffer (whole 128-byte units)
-    int store_tma;               // 1: output tiles leave by TMA store, 0: by plain stores
-    int *status;                 // set to 1 when a wait gives up
-};
-
-// work items: (plane, tile, R) with tile t of output plane `plane` (the CTA's tiles are
-// blockIdx.x, + gridDim.x, ... over all planes) and leading kernel index R whose input
-// plane q exists
-struct Item {
-    int plane, tile;
-    int64_t R, q;
-};
-
-// the first item at or after `it` (R included)
-__device__ __forceinline__ bool advance(const Params &cp, Item &it)
-{
-    while (it.plane < cp.planes) {
-        for (; it.R < cp.p.k_lead_total; ++it.R) {
-            it.q = lead_plane(cp.p, it.plane, it.R);
-            if (it.q >= 0) return true;
-        }
-        it.R = 0;
-        it.tile += gridDim.x;
-        while (it.tile >= cp.tiles_per_plane && it.plane < cp.planes) {
-            it.tile -= cp.tiles_per_plane;
-            ++it.plane;
-        }
-    }
-    return false;
-}
-
-// elected thread: the staged box of item (t, q) into `buf` (rows oy0 - (Kr - 1) ..,
-// columns ox0 - PADC ..; the copy engine zero-fills outside the input)
-template <int PADC>
-__device__ __forceinline__ void issue(const CUtensorMap *m, const Params &cp, const Item &it, float *buf,
-                                      uint64_t *bar)
-{
-    const int ty = it.tile / cp.tiles_x, tx = it.tile - ty * cp.tiles_x;
-    ft_tma::fence_proxy_async();
-    ft_tma::mbar_expect_tx(bar, (uint32_t)(cp.SH * (TW + PADC) * 4));
-    ft_tma::tma_load_3d(buf, m, tx * TW - PADC, ty * TH - ((int)cp.p.Kr - 1), (int)it.q, bar);
-}
-
-// A CTA walks tiles blockIdx.x, + gridDim.x, ... and, for each, the leading kernel
-// indices whose input plane exists (one work item each).  One elected thread brings the
-// next item's box into the other of two staging buffers while the CTA computes the
-// current one (completion tracked by an mbarrier with the box's byte count), so the
-// copies overlap the FMAs.  The arithmetic per item is that of conv_fma_kernel (three
-// branch-free phases of staged rows, OY rows x 4 columns per thread, kernel taps four
-// at a time from shared memory); all kernel slices are staged once.  Finished tiles go
-// out through a shared-memory staging tile, by TMA store when the output rows allow it.
-// Every wait is bounded: on expiry the CTA sets the status word, waits a bounded time
-// for its copy in flight, and returns.
-template <int NTAP>
-__global__ void __launch_bounds__(kThreads, NTAP <= 9 ? 3 : 2)
-conv_tma_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_map,
-                const Params cp)
-{
-    constexpr int PADC = (NTAP - 1 + 3) & ~3;
-    constexpr int BW = TW + PADC;
-    constexpr int KS = (NTAP + 3) & ~3;
-    extern __shared__ __align__(128) float smf[];
-    const ConvParams &p = cp.p;
-    const int tid = threadIdx.x;
-    const int Kr = (int)p.Kr, Kc = (int)p.Kc;
-    float *buf0 = smf, *buf1 = smf + cp.buf_floats;
-    float *so = smf + 2 * cp.buf_floats;
-    float *ks = so + TH * TW;
-    const int nk = (int)p.k_lead_total * Kr * KS;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(ks + ((nk + 3) & ~3));
-    // the copy engine writes 128-byte aligned boxes; refuse (and report) otherwise
-    if (ft_tma::smem_addr(smf) & 127) {
-        if (tid == 0) atomicExch(cp.status, 2);
-        return;
-    }
-    for (int i = tid; i < nk; i += kThreads) {
-        const int row = i / KS, b = i - row * KS;      // row = R * Kr + a
-        ks[i] = b < Kc ? __ldg(p.ker + (int64_t)row * Kc + b) : 0.f;
-    }
-    if (tid == 0) {
-        ft_tma::mbar_init(&bar[0], 1);
-        ft_tma::mbar_init(&bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    Item it{0, (int)blockIdx.x, 0, 0};
-    while (it.tile >= cp.tiles_per_plane && it.plane < cp.planes) {
-        it.tile -= cp.tiles_per_plane;
-        ++it.plane;
-    }
-    bool have = advance(cp, it);
-    if (tid == 0 && have) issue<PADC>(&in_map, cp, it, buf0, &bar[0]);
-
-    const int c0 = 4 * (tid & 31);
-    const int r0 = OY * (tid >> 5);
-    float acc[OY][4];
-#pragma unroll
-    for (int y = 0; y < OY; ++y)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[y][c] = 0.f;
-
-    for (int k = 0; have; ++k) {
-        Item nx = it;
-        ++nx.R;
-        const bool hn = advance(cp, nx);
-        float *cur = (k & 1) ? buf1 : buf0;
-        // the other buffer was released by the barrier that ended the previous item
-        if (tid == 0 && hn) issue<PADC>(&in_map, cp, nx, (k & 1) ? buf0 : buf1, &bar[(k + 1) & 1]);
-        const bool ok = ft_tma::mbar_wait(&bar[k & 1], (k >> 1) & 1);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicExch(cp.status, 1);
-                if (hn) ft_tma::mbar_wait(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1);
-                if (cp.store_tma) ft_tma::bulk_wait();
-            }
-            __syncthreads();
-            return;
-        }
-
-        const float4 *ks4 = reinterpret_cast<const float4 *>(ks + (int64_t)it.R * Kr * KS);
-        const float *base = cur + r0 * BW + c0;
-        float win[PADC + 4];
-#pragma unroll
-        for (int ir = 0; ir < OY - 1; ++ir) {
-            load_window<PADC>(win, base + ir * BW);
-#pragma unroll
-            for (int y = 0; y <= ir; ++y) fma_row<NTAP, PADC>(acc[y], win, ks4 + (y + Kr - 1 - ir) * (KS / 4));
-        }
-        for (int ir = OY - 1; ir < Kr; ++ir) {
-            load_window<PADC>(win, base + ir * BW);
-            const float4 *kb = ks4 + (Kr - 1 - ir) * (KS / 4);
-#pragma unroll
-            for (int y = 0; y < OY; ++y) fma_row<NTAP, PADC>(acc[y], win, kb + y * (KS / 4));
-        }
-#pragma unroll
-        for (int t3 = 1; t3 < OY; ++t3) {
-            load_window<PADC>(win, base + (Kr - 1 + t3) * BW);
-#pragma unroll
-            for (int y = t3; y < OY; ++y) fma_row<NTAP, PADC>(acc[y], win, ks4 + (y - t3) * (KS / 4));
-        }
-        __syncthreads();          // buffer `cur` is free for the copy issued next
-
-        if (!hn || nx.tile != it.tile || nx.plane != it.plane) {
-            // the tile is complete: out through the staging tile
-            const int plane = it.plane;
-            const int ty = it.tile / cp.tiles_x, tx = it.tile - ty * cp.tiles_x;
-            if (cp.store_tma && tid == 0) ft_tma::bulk_wait_read();   // the previous store has read `so`
-            __syncthreads();
-#pragma unroll
-            for (int y = 0; y < OY; ++y)
-                *reinterpret_cast<float4 *>(so + (r0 + y) * TW + c0) =
-                    make_float4(acc[y][0], acc[y][1], acc[y][2], acc[y][3]);
-            if (cp.store_tma) ft_tma::fence_proxy_async();
-            __syncthreads();
-            if (cp.store_tma) {
-                if (tid == 0) {
-                    ft_tma::tma_store_3d(&out_map, so, tx * TW, ty * TH, plane);
-                    ft_tma::bulk_commit();
-                }
-            } else {
-                // plain stores: a thread keeps one column (pair) and walks rows
-                const int64_t oy0 = (int64_t)ty * TH, ox0 = (int64_t)tx * TW;
-                const int rows = p.Mr - oy0 < TH ? (int)(p.Mr - oy0) : TH;
-                const int cols = p.Mc - ox0 < TW ? (int)(p.Mc - ox0) : TW;
-                float *dst = p.out + ((int64_t)plane * p.Mr + oy0) * p.Mc + ox0;
-                if (cp.store_tma == 0 && (p.Mc & 1) == 0 && (reinterpret_cast<uintptr_t>(p.out) & 7) == 0) {
-                    const int c = 2 * (tid & (TW / 2 - 1));
-                    if (c < cols) {
-                        for (int r = tid / (TW / 2); r < rows; r += kThreads / (TW / 2)) {
-                            const float2 v = *reinterpret_cast<const float2 *>(so + r * TW + c);
-                            if (c + 1 < cols) *reinterpret_cast<float2 *>(dst + r * p.Mc + c) = v;
-                            else dst[r * p.Mc + c] = v.x;
-                        }
-                    }
-                } else {
-                    const int c = tid & (TW - 1);
-                    if (c < cols)
-                        for (int r = tid / TW; r < rows; r += kThreads / TW) dst[r * p.Mc + c] = so[r * TW + c];
-                }
-            }
-#pragma unroll
-            for (int y = 0; y < OY; ++y)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[y][c] = 0.f;
-        }
-        it = nx;
-        have = hn;
-    }
-    if (cp.store_tma && tid == 0) ft_tma::bulk_wait();
-}
-
-}  // namespace conv_tma
-
-// 3-D fp32 map over `planes` planes of rows x cols (row-major, contiguous), box
-// bw x bh x 1
-bool f32_plane_map(CUtensorMap *m, const float *base, int64_t cols, int64_t rows, int64_t planes, int bw, int bh)
-{
-    PFN_cuTensorMapEncodeTiled_v12000 enc = ft::tensor_map_encoder();
-    if (!enc) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
-    const cuuint64_t strides[2] = {(cuuint64_t)(cols * 4), (cuuint64_t)(cols * rows * 4)};
-    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// the persistent TMA kernel when the input rows meet the copy engine's rules (16-byte
-// aligned base, row length a multiple of 4 floats) and the staging fits; *used = false
-// otherwise (the caller then takes conv_fma_kernel)
-template <int NTAP>
-ft_status launch_tma(const ConvParams &p, int64_t planes, cudaStream_t s, bool *used)
-{
-    using namespace conv_tma;
-    constexpr int PADC = (NTAP - 1 + 3) & ~3;
-    constexpr int BW = TW + PADC;
-    constexpr int KS = (NTAP + 3) & ~3;
-    *used = false;
-    if (!p.vec_in || p.Kr + TH - 1 > 256) return FT_OK;
-    int64_t in_planes = 1;
-    for (int d = 0; d < p.nlead; ++d) in_planes *= p.in_lead[d];
-    const int64_t tiles_y = ft::ceil_div(p.Mr, TH), tiles_x = ft::ceil_div(p.Mc, TW);
-    if (tiles_y * tiles_x * planes > 0x7fffffffLL) return FT_OK;
-    Params cp{};
-    cp.p = p;
-    cp.planes = (int)planes;
-    cp.tiles_x = (int)tiles_x;
-    cp.tiles_per_plane = (int)(tiles_x * tiles_y);
-    const int64_t total_tiles = planes * cp.tiles_per_plane;
-    cp.SH = TH + (int)p.Kr - 1;
-    cp.buf_floats = (cp.SH * BW + 31) / 32 * 32;
-    const int64_t nk = p.k_lead_total * p.Kr * KS;
-    const size_t smem = sizeof(float) * (2 * (size_t)cp.buf_floats + TH * TW + (size_t)((nk + 3) & ~3)) + 16;
-    if (smem > 200 * 1024) return FT_OK;
-    CUtensorMap in_map, out_map;
-    if (!f32_plane_map(&in_map, p.in, p.Nc, p.Nr, in_planes, BW, cp.SH)) return FT_OK;
-    cp.store_tma = (p.vec_out && f32_plane_map(&out_map, p.out, p.Mc, p.Mr, planes, TW, TH)) ? 1 : 0;
-    if (!cp.store_tma) out_map = in_map;            // unused
-    void *st = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&st, g_fastconv_status);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(conv_tma_kernel<NTAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)   // as much shared memory as the SM has: more resident CTAs
-        e = cudaFuncSetAttribute(conv_tma_kernel<NTAP>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-    int per_sm = 0, dev = 0, nsm = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<NTAP>, kThreads, smem);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) {
-        ft::set_cuda_error(e);
-        return FT_ERR_CUDA;
-    }
-    if (per_sm < 1) return FT_OK;
-    cp.status = static_cast<int *>(st);
-    const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)per_sm * nsm);
-    conv_tma_kernel<NTAP><<<(unsigned)grid, kThreads, smem, s>>>(in_map, out_map, cp);
-    *used = true;
-    return ft::check_launch();
-}
-
 // 64-row tiles (kernels up to 9 columns, whose registers allow them) need Kr >= 8 and
 // enough tiles for two CTAs per SM; else 32-row tiles
 template <int NTAP>
 ft_status launch_fma_oy(const ConvParams &p, int64_t planes, cudaStream_t s)
 {
-    bool used = false;
-    const ft_status st = launch_tma<NTAP>(p, planes, s, &used);
-    if (st != FT_OK || used) return st;
     if constexpr (NTAP <= 9) {
         if (p.Kr < 8) return launch_fma<NTAP, 4>(p, planes, s);
         int dev = 0, nsm = 0;
@@ -953,7 +602,9 @@ ft_status launch_fma_oy(const ConvParams &p, int64_t planes, cudaStream_t s)
 ft_status launch_fma_taps(const ConvParams &p, int64_t planes, cudaStream_t s)
 {
     switch (p.Kc / 2) {
-    case 0: case 1: case 2: return launch_fma_oy<5>(p, planes, s);
+    case 0: return launch_fma_oy<1>(p, planes, s);
+    case 1: return launch_fma_oy<3>(p, planes, s);
+    case 2: return launch_fma_oy<5>(p, planes, s);
     case 3: return launch_fma_oy<7>(p, planes, s);
     case 4: return launch_fma_oy<9>(p, planes, s);
     case 5: return launch_fma_oy<11>(p, planes, s);
@@ -987,9 +638,8 @@ extern "C" ft_status fastconv_out_dims(int nd, const int64_t *dims, const int64_
     return FT_OK;
 }
 
-extern "C" ft_status fastconv_nd(const float *input, const int64_t *dims, int nd,
-                                 const float *kernel, const int64_t *kdims, float *out,
-                                 void *stream)
+static ft_status conv_nd_impl(const float *input, const int64_t *dims, int nd, const float *kernel,
+                              const int64_t *kdims, float *out, cudaStream_t s)
 {
     if (!input || !dims || !kernel || !kdims || !out) return FT_ERR_INVALID_ARG;
     int64_t odims[FT_MAX_NDIM];
@@ -1029,7 +679,6 @@ extern "C" ft_status fastconv_nd(const float *input, const int64_t *dims, int nd
     p.vec_in = ((reinterpret_cast<uintptr_t>(input) & 15) == 0 && (p.Nc & 3) == 0) ? 1 : 0;
     p.vec_out = ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && (p.Mc & 3) == 0) ? 1 : 0;
 
-    cudaStream_t s = ft::as_stream(stream);
     const bool tiled = p.Kc <= 65 && p.Kr <= 129;
     if (!tiled) {
         if (tot_out / 256 + 1 > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
@@ -1043,21 +692,107 @@ extern "C" ft_status fastconv_nd(const float *input, const int64_t *dims, int nd
         return launch_rows_kl<2>(p, planes, s);
     }
     if (p.Mr == 1) return launch_by_pad<1, 8>(p, planes, s);          // rank 1 (one row)
+    if (p.Kc <= 17) {
+        // persistent TMA-fed kernel when the input rows allow it, else (4+ rows) the
+        // cp.async-staged kernel
+        bool used = false;
+        const ft_status st = launch_conv_tma(p, planes, s, &used);
+        if (st != FT_OK || used) return st;
+        if (p.Kr >= 4) return launch_fma_taps(p, planes, s);
+    }
     if (p.Kr * p.Kc <= 16) return launch_by_pad<4, 1>(p, planes, s);  // small, memory-bound
-    if (p.Kr >= 4 && p.Kc <= 17) return launch_fma_taps(p, planes, s); // FMA-bound
     return launch_by_pad<8, 1>(p, planes, s);                           // wide or flat kernels
 }
 
-extern "C" ft_status fastconv_check(void *stream)
+extern "C" ft_status fastconv_nd(const float *input, const int64_t *dims, int nd,
+                                 const float *kernel, const int64_t *kdims, float *out,
+                                 void *stream)
 {
-    int v = 0;
-    const int zero = 0;
-    cudaError_t e = cudaStreamSynchronize(ft::as_stream(stream));
-    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&v, g_fastconv_status, sizeof(int));
-    if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_fastconv_status, &zero, sizeof(int));
-    if (e != cudaSuccess) {
-        ft::set_cuda_error(e);
-        return FT_ERR_CUDA;
+    return conv_nd_impl(input, dims, nd, kernel, kdims, out, ft::as_stream(stream));
+}
+
+// Separable kernel k = f_0 (x) f_1 (x) ... : one 1-D full convolution per axis, each a
+// plane pass of the tiled kernels with a kernel of one row or one column (the work per
+// output drops from prod(K) to sum(K) multiply-adds).
+extern "C" ft_status fastconv_separable(const float *input, const int64_t *dims, int nd,
+                                        const float *const *factors, const int64_t *kdims, float *out,
+                                        float *scratch, void *stream)
+{
+    if (!input || !dims || !factors || !kdims || !out) return FT_ERR_INVALID_ARG;
+    int64_t odims[FT_MAX_NDIM];
+    ft_status st = fastconv_out_dims(nd, dims, kdims, odims);
+    if (st != FT_OK) return st;
+    for (int d = 0; d < nd; ++d)
+        if (!factors[d]) return FT_ERR_INVALID_ARG;
+    if (nd >= 2 && !scratch) return FT_ERR_INVALID_ARG;
+    if (scratch == input || scratch == out || out == input) return FT_ERR_INVALID_ARG;
+    cudaStream_t s = ft::as_stream(stream);
+    int64_t cur[FT_MAX_NDIM];
+    for (int d = 0; d < nd; ++d) cur[d] = dims[d];
+    const float *src = input;
+    for (int d = 0; d < nd; ++d) {
+        float *dst = ((nd - 1 - d) % 2 == 0) ? out : scratch;     // the last pass writes `out`
+        int64_t outer = 1, inner = 1;
+        for (int e = 0; e < d; ++e) outer *= cur[e];
+        for (int e = d + 1; e < nd; ++e) inner *= cur[e];
+        if (inner == 1) {
+            const int64_t pd[2] = {outer, cur[d]}, pk[2] = {1, kdims[d]};
+            st = conv_nd_impl(src, pd, 2, factors[d], pk, dst, s);
+        } else {
+            const int64_t pd[3] = {outer, cur[d], inner}, pk[3] = {1, kdims[d], 1};
+            st = conv_nd_impl(src, pd, 3, factors[d], pk, dst, s);
+        }
+        if (st != FT_OK) return st;
+        cur[d] += kdims[d] - 1;
+        src = dst;
     }
-    return v ? FT_ERR_TIMEOUT : FT_OK;
+    return FT_OK;
+}
+
+// Rank-1 test of a host kernel: the fibres through its largest entry, scaled, are the
+// factors when their outer product reproduces the kernel to rel_tol * max |k|.
+extern "C" int fastconv_factor(const float *kernel, const int64_t *kdims, int nd, double rel_tol, float *factors)
+{
+    if (!kernel || !kdims || !factors || nd < 1 || nd > FT_MAX_NDIM || !(rel_tol >= 0.0)) return -1;
+    int64_t total = 1, stride[FT_MAX_NDIM];
+    for (int d = nd - 1; d >= 0; --d) {
+        if (kdims[d] < 1 || kdims[d] > ((int64_t)1 << 20)) return -1;
+        stride[d] = total;
+        total *= kdims[d];
+        if (total > ((int64_t)1 << 26)) return -1;
+    }
+    int64_t m = 0;
+    double vmax = 0.0;
+    for (int64_t i = 0; i < total; ++i)
+        if (std::fabs((double)kernel[i]) > vmax) {
+            vmax = std::fabs((double)kernel[i]);
+            m = i;
+        }
+    int64_t off[FT_MAX_NDIM + 1];
+    off[0] = 0;
+    for (int d = 0; d < nd; ++d) off[d + 1] = off[d] + kdims[d];
+    if (vmax == 0.0) {                   // the zero kernel: zero factors
+        for (int64_t i = 0; i < off[nd]; ++i) factors[i] = 0.f;
+        return 1;
+    }
+    const double v = (double)kernel[m];
+    int64_t mi[FT_MAX_NDIM];
+    for (int d = 0; d < nd; ++d) mi[d] = (m / stride[d]) % kdims[d];
+    // factor d: the fibre along d through the largest entry; the first factor also
+    // carries 1 / v^(nd-1) (the product of the fibres counts v nd times)
+    double scale = 1.0;
+    for (int d = 1; d < nd; ++d) scale /= v;
+    std::vector<double> f((size_t)off[nd]);
+    for (int d = 0; d < nd; ++d)
+        for (int64_t i = 0; i < kdims[d]; ++i) {
+            const double x = kernel[m + (i - mi[d]) * stride[d]];
+            f[(size_t)(off[d] + i)] = d == 0 ? x * scale : x;
+        }
+    for (int64_t i = 0; i < total; ++i) {
+        double prod = 1.0;
+        for (int d = 0; d < nd; ++d) prod *= f[(size_t)(off[d] + (i / stride[d]) % kdims[d])];
+        if (std::fabs(prod - (double)kernel[i]) > rel_tol * vmax) return 0;
+    }
+    for (int64_t i = 0; i < off[nd]; ++i) factors[i] = (float)f[(size_t)i];
+    return 1;
 }

@@ -191,6 +191,49 @@ ttc_derivatives_kernel(const T0 *fa, const T0 *fb, int H, int W, int64_t pitch_e
     if (G) G[o] = fmaf((float)j + xoff, ex, ((float)i + yoff) * ey);
 }
 
+// Gradient magnitude and direction of one image (Sec. II, Eq. Emag, Eq. Eangle): a
+// thread owns one output column and walks GR_ROWS output rows, keeping the previous
+// pixel row in registers; the right neighbour pixel comes from the next lane (the last
+// lane of a warp loads its own).  Stores are coalesced rows; HBM-bound.
+constexpr int GR_ROWS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+ttc_gradient_kernel(const T *__restrict__ img, int H, int W, int64_t pitch_e, float *__restrict__ mag,
+                    float *__restrict__ dir)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 256 + threadIdx.x;      // output column
+    const int i0 = blockIdx.y * GR_ROWS;               // first output row
+    const bool inside = j < W - 1;
+    const int jc = inside ? j : W - 2;                 // clamped column for loads
+    const int nrows = min(GR_ROWS, H - 1 - i0);        // output rows of this block (>= 1)
+    const bool own = lane == 31 || jc + 1 >= W - 1;    // the right neighbour is not in the next lane
+    // all pixel loads first (rows i0 .. i0 + nrows; rows past the image repeat the last)
+    float c0[GR_ROWS + 1], c1[GR_ROWS + 1];
+#pragma unroll
+    for (int r = 0; r <= GR_ROWS; ++r) {
+        const T *row = img + (int64_t)(i0 + min(r, nrows)) * pitch_e;
+        c0[r] = (float)__ldg(row + jc);
+        c1[r] = own ? (float)__ldg(row + jc + 1) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r <= GR_ROWS; ++r) {
+        const float n = __shfl_down_sync(0xffffffffu, c0[r], 1);
+        if (!own) c1[r] = n;
+    }
+#pragma unroll
+    for (int r = 0; r < GR_ROWS; ++r) {
+        const float ex = 0.5f * ((c1[r] - c0[r]) + (c1[r + 1] - c0[r + 1]));
+        const float ey = 0.5f * ((c0[r + 1] - c0[r]) + (c1[r + 1] - c1[r]));
+        if (inside && r < nrows) {
+            const int64_t o = (int64_t)(i0 + r) * (W - 1) + j;
+            if (mag) mag[o] = sqrtf(ex * ex + ey * ey);
+            if (dir) dir[o] = atan2f(ey, ex);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1165,6 +1208,24 @@ extern "C" ft_status ttc_derivatives(const void *prev, const void *cur, int dtyp
         ttc_derivatives_kernel<float><<<grid, 256, 0, s>>>(
             static_cast<const float *>(prev), static_cast<const float *>(cur), H, W, pitch_bytes / 4, xoff,
             yoff, Ex, Ey, Et, G);
+    return ft::check_launch();
+}
+
+extern "C" ft_status ttc_gradient(const void *image, int dtype, int H, int W, int64_t pitch_bytes, float *mag,
+                                  float *dir, void *stream)
+{
+    if (!image || (!mag && !dir)) return FT_ERR_INVALID_ARG;
+    const ft_status st = check_frames(dtype, H, W, pitch_bytes);
+    if (st != FT_OK) return st;
+    const dim3 grid((unsigned)ft::ceil_div(W - 1, 256), (unsigned)ft::ceil_div(H - 1, GR_ROWS));
+    if (grid.y > 65535) return FT_ERR_UNSUPPORTED;
+    cudaStream_t s = ft::as_stream(stream);
+    if (dtype == FT_U8)
+        ttc_gradient_kernel<unsigned char><<<grid, 256, 0, s>>>(static_cast<const unsigned char *>(image), H, W,
+                                                                pitch_bytes, mag, dir);
+    else
+        ttc_gradient_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(image), H, W, pitch_bytes / 4,
+                                                        mag, dir);
     return ft::check_launch();
 }
 

@@ -166,3 +166,42 @@ def test_pyramid_layout_and_pair_desc(L):
     text = open(os.path.join(ROOT, "include", "fastttc.h")).read()
     assert "const void *prev_pyramid;" in text and "void *cur_pyramid;" in text
     assert ctypes.sizeof(ft.PairDesc) == 48 and ft.PairDesc.cur_pyramid.offset == 40
+
+
+def test_fastconv_factor_rank_one_test(L):
+    """Separable kernels (Gaussian, Sobel, 3-D box) factor and their factors' outer
+    product reproduces the kernel; general kernels do not factor; bad arguments -1."""
+    g1 = np.exp(-0.5 * ((np.arange(7) - 3) / 1.3) ** 2)
+    gauss = np.outer(g1, g1).astype(np.float32)
+    sobel = np.array([[1, 0, -1], [2, 0, -2], [1, 0, -1]], np.float32)
+    box = np.full((3, 4, 5), 1.0 / 60, np.float32)
+    for k in (gauss, sobel, box, np.array([2.5, -1.0, 0.25], np.float32)):
+        f = ft.factor_kernel(k, rel_tol=1e-6)
+        assert f is not None and [len(x) for x in f] == list(k.shape)
+        prod = f[0].astype(np.float64)
+        for x in f[1:]:
+            prod = np.multiply.outer(prod, x.astype(np.float64))
+        np.testing.assert_allclose(prod, k, atol=2e-6 * np.abs(k).max())
+    rng = np.random.default_rng(3)
+    assert ft.factor_kernel(rng.standard_normal((5, 5)).astype(np.float32)) is None
+    assert ft.factor_kernel(np.eye(3, dtype=np.float32)) is None
+    z = ft.factor_kernel(np.zeros((2, 3), np.float32))
+    assert z is not None and not any(x.any() for x in z)
+    f = (ctypes.c_float * 4)()
+    k = (ctypes.c_float * 4)(1, 2, 3, 4)
+    dims = (ctypes.c_int64 * 2)(2, 2)
+    assert L.fastconv_factor(None, dims, 2, 1e-6, f) == -1
+    assert L.fastconv_factor(k, dims, 0, 1e-6, f) == -1
+    assert L.fastconv_factor(k, dims, 2, -1.0, f) == -1
+
+
+def test_fastconv_separable_validation(L):
+    f = ctypes.c_void_p(16)
+    dims = (ctypes.c_int64 * 2)(8, 8)
+    kd = (ctypes.c_int64 * 2)(3, 3)
+    facs = (ctypes.c_void_p * 2)(16, None)
+    assert L.fastconv_separable(f, dims, 2, facs, kd, f, ctypes.c_void_p(32), None) == 1   # null factor
+    facs = (ctypes.c_void_p * 2)(16, 16)
+    assert L.fastconv_separable(f, dims, 2, facs, kd, ctypes.c_void_p(48), None, None) == 1  # no scratch
+    assert L.fastconv_separable(f, dims, 2, facs, kd, ctypes.c_void_p(48), ctypes.c_void_p(48), None) == 1
+    assert L.fastconv_separable(f, dims, 9, facs, kd, ctypes.c_void_p(48), ctypes.c_void_p(64), None) == 2

@@ -145,11 +145,12 @@ def test_fastconv_full_size_3d_sampled(kk):
 
 @pytest.mark.parametrize("kc", list(range(2, 18)))
 def test_fastconv_fma_kernel_every_width(kc):
-    """The FMA-bound kernel for every kernel width it serves (2..17 columns, 4 or more
-    rows): rows equal to the tile's rows per thread (middle phase of length one) and
+    """The FMA-bound kernels for every kernel width they serve (2..17 columns): rows equal to the tile's rows per thread (middle phase of length one) and
     longer; several 128-column tiles with a ragged tail; a width that is not a
-    multiple of 4 and an offset base (scalar staging); two planes."""
-    for kr in (4, 9):
+    multiple of 4 and an offset base (scalar staging); two planes.  Kernels of 1-3 rows
+    take the copy-engine kernel's small-row schedule (or the tile kernel when the rows
+    are not addressable by the copy engine)."""
+    for kr in (1, 2, 3, 4, 9):
         k = scenes.normal_array((kr, kc), seed=100 + kc + kr)
         _check_full(scenes.uniform_array((45, 600), seed=kc), k)
         _check_full(scenes.uniform_array((37, 531), seed=kc + 1), k)
@@ -184,3 +185,38 @@ def test_fastconv_tma_kernel_leading_dims(shape, kshape):
     E = scenes.uniform_array(shape, seed=sum(shape))
     k = scenes.normal_array(kshape, seed=sum(kshape))
     _check_full(E, k)
+
+
+@pytest.mark.parametrize("shape,klens", [
+    ((37, 531), (7, 5)), ((300,), (9,)), ((5, 33, 128), (3, 5, 7)), ((2, 3, 17, 36), (2, 1, 6, 7)),
+    ((64, 64), (1, 17)), ((40, 100), (33, 1)),
+])
+def test_fastconv_separable_matches_full_conv(shape, klens):
+    """One 1-D pass per axis equals the full convolution with the outer-product kernel."""
+    E = scenes.uniform_array(shape, seed=sum(shape))
+    facs = [scenes.normal_array((k,), seed=10 + i) for i, k in enumerate(klens)]
+    k = facs[0].astype(np.float64)
+    for f in facs[1:]:
+        k = np.multiply.outer(k, f.astype(np.float64))
+    dev = torch.device("cuda")
+    got = ft.fastconv_separable(torch.from_numpy(E).to(dev), [torch.from_numpy(f).to(dev) for f in facs])
+    ft.fastconv_check()
+    ref, rabs = oracle.fastconv_nd(E, k, with_abs=True)
+    err = np.abs(got.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(err <= REL * rabs + 1e-30), float(np.max(err / np.maximum(rabs, 1e-30)))
+
+
+def test_fastconv_separable_full_size_gaussian_sampled():
+    """1080x1920 conv 15x15 normalised Gaussian through the factored path, sampled."""
+    E = scenes.uniform_array((1080, 1920), seed=2024)
+    k = scenes.gaussian_kernel(15)
+    facs = ft.factor_kernel(k, rel_tol=1e-6)
+    assert facs is not None
+    dev = torch.device("cuda")
+    got = ft.fastconv_separable(torch.from_numpy(E).to(dev), [torch.from_numpy(f).to(dev) for f in facs])
+    got = got.cpu().numpy()
+    pts = np.random.default_rng(5).integers(0, got.size, 3000).astype(np.int64)
+    ref, rabs = oracle.fastconv_points(E, k, pts)
+    g = got.reshape(-1)[pts].astype(np.float64)
+    # the factors carry the rank-1 test's rounding (1e-6 of the largest tap)
+    assert np.all(np.abs(g - ref) <= 2e-5 * rabs + 1e-30)

@@ -275,3 +275,53 @@ def test_full_size_video_large_tile_paths():
         for l in range(5):
             check_record(one[l], ref[l], 1, l)
     ctx.close()
+
+
+def _gradient_check(E, got_mag, got_dir, integer):
+    """|E| to 1.2e-7 relative for uint8 (Ex, Ey exact), direction to 1e-6 rad (atan2f
+    is within 2 ulp); float frames add the FP32 rounding of the differences,
+    1e-6 of the block's absolute sum, propagated to the direction through 1/|E|."""
+    mag, ang = oracle.gradient(E)
+    E = np.asarray(E, np.float64)
+    blk = np.abs(E[:-1, :-1]) + np.abs(E[:-1, 1:]) + np.abs(E[1:, :-1]) + np.abs(E[1:, 1:])
+    dm = np.abs(got_mag.astype(np.float64) - mag)
+    bound_m = 1.2e-7 * mag + (0.0 if integer else 1e-6 * blk)
+    assert np.all(dm <= bound_m + 1e-30), float(np.max(dm - bound_m))
+    d = np.abs(np.angle(np.exp(1j * (got_dir.astype(np.float64) - ang))))
+    ok = mag > 0
+    bound_d = 1e-6 + (np.zeros_like(mag) if integer else 1e-6 * blk / np.maximum(mag, 1e-300))
+    assert np.all(d[ok] <= bound_d[ok]), float(np.max(d[ok] - bound_d[ok]))
+    assert np.all(np.abs(got_dir) <= np.float32(np.pi))
+
+
+def test_gradient_matches_oracle_uint8_full_size():
+    sc = scenes.tilted_plane_scene(H=1080, W=1920, seed=21)
+    img = scenes.render(sc, 3.0)
+    mag, ang = ft.gradient(img.to(DEV))
+    _gradient_check(img.numpy(), mag.cpu().numpy(), ang.cpu().numpy(), True)
+
+
+@pytest.mark.parametrize("H,W,pad,offset", [(37, 53, 3, 0), (2, 2, 0, 0), (9, 300, 0, 1), (70, 33, 5, 1)])
+def test_gradient_odd_shapes_pitch_and_dtypes(H, W, pad, offset):
+    rng = np.random.default_rng(H * W)
+    for integer in (True, False):
+        E = (rng.integers(0, 256, (H, W)) if integer else rng.standard_normal((H, W))).astype(
+            np.uint8 if integer else np.float32)
+        buf = torch.zeros((H * (W + pad) + offset,), dtype=torch.uint8 if integer else torch.float32, device=DEV)
+        view = buf[offset:].view(H, W + pad)[:, :W]
+        view.copy_(torch.from_numpy(E))
+        mag, ang = ft.gradient(view)
+        _gradient_check(E, mag.cpu().numpy(), ang.cpu().numpy(), integer)
+    # one output only
+    m_only, none = ft.gradient(view, with_dir=False)
+    assert none is None and torch.equal(m_only, mag)
+
+
+def test_gradient_errors():
+    L = ft.load()
+    x = torch.zeros((4, 4), dtype=torch.uint8, device=DEV)
+    out = torch.empty((3, 3), device=DEV)
+    assert L.ttc_gradient(x.data_ptr(), 0, 4, 4, 4, None, None, None) == 1
+    assert L.ttc_gradient(x.data_ptr(), 0, 1, 4, 4, out.data_ptr(), None, None) == 2
+    assert L.ttc_gradient(x.data_ptr(), 0, 4, 4, 3, out.data_ptr(), None, None) == 2
+    assert L.ttc_gradient(x.data_ptr(), 7, 4, 4, 4, out.data_ptr(), None, None) == 1
