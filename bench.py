@@ -212,6 +212,34 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
         rows.append({"input": list(shape), "kernel": list(kshape), "us": t * 1e6, "bound": bound,
                      "GBps": gbs, "hbm_frac": gbs / hbm_peak, "GFLOPps": flops / t / 1e9,
                      "fma_frac": flops / t / fma_peak, "algorithmic_bytes": byts, "flops": flops})
+    # inputs of other element types, staged by the copy engine in their own type and
+    # widened in the kernel: bytes = input bytes + FP32 output
+    for shape, kshape, dt in (((16, 1080, 1920), (1, 3, 3), torch.uint8), ((16, 1080, 1920), (1, 7, 7), torch.uint8),
+                              ((16, 1080, 1920), (1, 5, 5), torch.float16)):
+        Ef = torch.from_numpy(scenes.uniform_array(shape, seed=2024)).to(dev)
+        E = (Ef * 255).to(torch.uint8) if dt == torch.uint8 else Ef.to(dt)
+        k = torch.from_numpy(scenes.gaussian_kernel(kshape[-1]).reshape(kshape)).to(dev)
+        out = ft.fastconv_nd(E, k)
+        ts = []
+        for i in range(reps + 2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            ft.fastconv_nd(E, k, out=out)
+            e1.record(s)
+            ts.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        launches += reps + 2
+        t = float(np.median([a.elapsed_time(b) for a, b in ts[2:]])) * 1e-3
+        byts = E.numel() * E.element_size() + 4 * (out.numel() + k.numel())
+        flops = 2.0 * E.numel() * k.numel()
+        bound = "fma" if flops / byts > fma_peak / (hbm_peak * 1e9) else "hbm"
+        rows.append({"input": list(shape), "kernel": list(kshape), "input_dtype": str(dt).replace("torch.", ""),
+                     "us": t * 1e6, "bound": bound, "GBps": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / hbm_peak,
+                     "GFLOPps": flops / t / 1e9, "fma_frac": flops / t / fma_peak, "algorithmic_bytes": byts,
+                     "flops": flops})
+
     # separable kernels through one 1-D pass per axis (normalised Gaussians): time and
     # the speedup over the direct path for the same output
     def timed(fn):

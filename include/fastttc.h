@@ -83,6 +83,20 @@ ft_status fastconv_nd(const float *input, const int64_t *dims, int nd,
                       const float *kernel, const int64_t *kdims, float *out, void *stream);
 
 /*
+ * fastconv_nd for inputs of other element types (Sec. IV-C: FastConv covers many signal
+ * types): in_dtype FT_U8, FT_I16, FT_F16, FT_BF16 (or FT_F32, which is fastconv_nd).
+ * The kernel and the output stay FP32; every input value is widened to FP32 exactly.
+ * Planes of more than one row with kernels of at most 17 columns whose input rows are
+ * 16-byte aligned whole 16-byte units are staged in the input's own type by the copy
+ * engine and widened in the kernel; any other request converts the input into
+ * `scratch` (device, prod(dims) floats) first and runs the FP32 path.
+ * Errors: as fastconv_nd; FT_ERR_INVALID_ARG (bad in_dtype), FT_ERR_WORKSPACE (scratch
+ * needed but NULL).
+ */
+ft_status fastconv_nd_typed(const void *input, int in_dtype, const int64_t *dims, int nd, const float *kernel,
+                            const int64_t *kdims, float *out, float *scratch, void *stream);
+
+/*
  * Full n-D convolution with a separable kernel k = f_0 (x) f_1 (x) ... (x) f_{nd-1}
  * (outer product of one vector per axis; the paper's Future Work: directional
  * derivatives, Gaussians and block averages are separable): one 1-D full convolution
@@ -122,7 +136,8 @@ ft_status fastconv_check(void *stream);
 /* Time to contact (Sec. V-A, V-B)                                           */
 /* ------------------------------------------------------------------------ */
 
-typedef enum { FT_U8 = 0, FT_F32 = 1 } ft_dtype;   /* frame pixel type */
+/* element types: frames (FT_U8, FT_F32) and FastConv inputs (all five) */
+typedef enum { FT_U8 = 0, FT_F32 = 1, FT_I16 = 2, FT_F16 = 3, FT_BF16 = 4 } ft_dtype;
 typedef enum { FT_MODE_TTC = 0, FT_MODE_FOE = 1 } ft_mode;
 
 /* Per-result flags (information, not errors). */

@@ -86,6 +86,8 @@ def load(path: Optional[str] = None):
     L.fastconv_out_dims.restype = st
     L.fastconv_nd.argtypes = [_vp, _i64p, ctypes.c_int, _vp, _i64p, _vp, _vp]
     L.fastconv_nd.restype = st
+    L.fastconv_nd_typed.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_int, _vp, _i64p, _vp, _vp, _vp]
+    L.fastconv_nd_typed.restype = st
     L.fastconv_check.argtypes = [_vp]
     L.fastconv_check.restype = st
     L.fastconv_separable.argtypes = [_vp, _i64p, ctypes.c_int, ctypes.POINTER(_vp), _i64p, _vp, _vp, _vp]
@@ -178,13 +180,20 @@ def fastconv_out_dims(dims: Sequence[int], kdims: Sequence[int]) -> tuple:
     return tuple(int(out[i]) for i in range(nd))
 
 
+CONV_DTYPES = {torch.uint8: 0, torch.float32: 1, torch.int16: 2, torch.float16: 3, torch.bfloat16: 4}
+
+
 def fastconv_nd(x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Full n-D convolution of x with k (FP32, Eq. conv2 read as the full linear convolution)."""
+    """Full n-D convolution of x with k (Eq. conv2 read as the full linear convolution).
+
+    x: float32, uint8, int16, float16 or bfloat16 (widened to FP32 exactly); k and the
+    output are float32."""
     L = load()
     _require_cuda(x, "x")
     _require_cuda(k, "k")
-    if x.dtype != torch.float32 or k.dtype != torch.float32:
-        raise ValueError("fastconv_nd takes float32 tensors")
+    if x.dtype not in CONV_DTYPES or k.dtype != torch.float32:
+        raise ValueError("fastconv_nd takes a float32 kernel and a float32, uint8, int16, float16 or "
+                         "bfloat16 input")
     if x.dim() != k.dim():
         raise ValueError("x and k must have the same rank")
     x = x.contiguous()
@@ -194,8 +203,18 @@ def fastconv_nd(x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = 
         out = torch.empty(od, dtype=torch.float32, device=x.device)
     elif tuple(out.shape) != od or not out.is_contiguous() or out.dtype != torch.float32:
         raise ValueError("out has the wrong shape, dtype or layout")
-    _check(L.fastconv_nd(x.data_ptr(), _dims(x.shape), x.dim(), k.data_ptr(), _dims(k.shape),
-                         out.data_ptr(), _stream_ptr(x)), "fastconv_nd")
+    if x.dtype == torch.float32:
+        _check(L.fastconv_nd(x.data_ptr(), _dims(x.shape), x.dim(), k.data_ptr(), _dims(k.shape),
+                             out.data_ptr(), _stream_ptr(x)), "fastconv_nd")
+        return out
+    args = (x.data_ptr(), CONV_DTYPES[x.dtype], _dims(x.shape), x.dim(), k.data_ptr(), _dims(k.shape),
+            out.data_ptr())
+    st = L.fastconv_nd_typed(*args, None, _stream_ptr(x))
+    if st == 4:                         # this request converts the input first: give it room
+        scratch = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+        st = L.fastconv_nd_typed(*args, scratch.data_ptr(), _stream_ptr(x))
+        out._fastconv_scratch = scratch  # alive until the caller drops `out`
+    _check(st, "fastconv_nd_typed")
     return out
 
 

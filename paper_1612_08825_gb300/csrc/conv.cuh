@@ -20,6 +20,8 @@ struct ConvParams {
     int64_t tiles_x, tiles_per_plane;
     int vec_in;                          // 1: input rows allow 16-byte loads
     int vec_out;                         // 1: output rows allow 16-byte stores
+    const void *in_t;                    // input of another element type (FT_U8, FT_I16, FT_F16, FT_BF16)
+    int in_dtype;                        // element type of in_t
 };
 
 // input plane feeding output plane `plane` through leading kernel index R, or -1 when
@@ -79,7 +81,13 @@ __device__ __forceinline__ void load_window(float (&win)[PADC + 4], const float 
 }
 
 // the persistent TMA-fed kernel for kernels of at most 17 columns when the input rows
-// meet the copy engine's rules; *used = false otherwise
+// meet the copy engine's rules; *used = false otherwise.  launch_conv_tma reads p.in
+// (FP32); the typed launchers read p.in_t (their element type).
 ft_status launch_conv_tma(const ConvParams &p, int64_t planes, cudaStream_t s, bool *used);
+ft_status launch_conv_tma_u8(const ConvParams &p, int64_t planes, cudaStream_t s, bool *used);
+ft_status launch_conv_tma_16(const ConvParams &p, int64_t planes, cudaStream_t s, bool *used);
+
+// device address of the FastConv status word (set when a bounded wait gives up)
+int *fastconv_status_word();
 
 }  // namespace ft_conv

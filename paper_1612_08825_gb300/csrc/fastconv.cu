@@ -24,6 +24,9 @@
 #include <cstdio>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "conv.cuh"
 
 namespace {
@@ -638,8 +641,9 @@ extern "C" ft_status fastconv_out_dims(int nd, const int64_t *dims, const int64_
     return FT_OK;
 }
 
-static ft_status conv_nd_impl(const float *input, const int64_t *dims, int nd, const float *kernel,
-                              const int64_t *kdims, float *out, cudaStream_t s)
+// plane decomposition of a rank-nd full convolution (shared by every entry point)
+static ft_status make_conv_params(const void *input, const int64_t *dims, int nd, const float *kernel,
+                                  const int64_t *kdims, float *out, ConvParams &p, int64_t &planes, int64_t &tot_out)
 {
     if (!input || !dims || !kernel || !kdims || !out) return FT_ERR_INVALID_ARG;
     int64_t odims[FT_MAX_NDIM];
@@ -647,7 +651,8 @@ static ft_status conv_nd_impl(const float *input, const int64_t *dims, int nd, c
     if (st != FT_OK) return st;
     // overflow guard: every size must stay below 2^62
     const int64_t lim = (int64_t)1 << 62;
-    int64_t tot_in = 1, tot_k = 1, tot_out = 1;
+    int64_t tot_in = 1, tot_k = 1;
+    tot_out = 1;
     for (int d = 0; d < nd; ++d) {
         if (odims[d] > lim / tot_out || dims[d] > lim / tot_in || kdims[d] > lim / tot_k)
             return FT_ERR_UNSUPPORTED;
@@ -655,14 +660,13 @@ static ft_status conv_nd_impl(const float *input, const int64_t *dims, int nd, c
         tot_k *= kdims[d];
         tot_out *= odims[d];
     }
-
-    ConvParams p{};
-    p.in = input;
+    p = ConvParams{};
+    p.in = static_cast<const float *>(input);
     p.ker = kernel;
     p.out = out;
     p.nlead = nd >= 2 ? nd - 2 : 0;
     p.k_lead_total = 1;
-    int64_t planes = 1;
+    planes = 1;
     for (int d = 0; d < p.nlead; ++d) {
         p.in_lead[d] = dims[d];
         p.k_lead[d] = kdims[d];
@@ -678,7 +682,16 @@ static ft_status conv_nd_impl(const float *input, const int64_t *dims, int nd, c
     p.Mc = odims[nd - 1];
     p.vec_in = ((reinterpret_cast<uintptr_t>(input) & 15) == 0 && (p.Nc & 3) == 0) ? 1 : 0;
     p.vec_out = ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && (p.Mc & 3) == 0) ? 1 : 0;
+    return FT_OK;
+}
 
+static ft_status conv_nd_impl(const float *input, const int64_t *dims, int nd, const float *kernel,
+                              const int64_t *kdims, float *out, cudaStream_t s)
+{
+    ConvParams p;
+    int64_t planes = 0, tot_out = 0;
+    const ft_status st0 = make_conv_params(input, dims, nd, kernel, kdims, out, p, planes, tot_out);
+    if (st0 != FT_OK) return st0;
     const bool tiled = p.Kc <= 65 && p.Kr <= 129;
     if (!tiled) {
         if (tot_out / 256 + 1 > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
@@ -709,6 +722,59 @@ extern "C" ft_status fastconv_nd(const float *input, const int64_t *dims, int nd
                                  void *stream)
 {
     return conv_nd_impl(input, dims, nd, kernel, kdims, out, ft::as_stream(stream));
+}
+
+namespace {
+
+template <typename T> __device__ __forceinline__ float widen(T v) { return (float)v; }
+template <> __device__ __forceinline__ float widen(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// exact conversion of n elements to FP32 (the fallback of fastconv_nd_typed)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) widen_kernel(const T *__restrict__ in, int64_t n, float *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        out[i] = widen(in[i]);
+}
+
+}  // namespace
+
+extern "C" ft_status fastconv_nd_typed(const void *input, int in_dtype, const int64_t *dims, int nd,
+                                       const float *kernel, const int64_t *kdims, float *out, float *scratch,
+                                       void *stream)
+{
+    cudaStream_t s = ft::as_stream(stream);
+    if (in_dtype == FT_F32) return conv_nd_impl(static_cast<const float *>(input), dims, nd, kernel, kdims, out, s);
+    if (in_dtype != FT_U8 && in_dtype != FT_I16 && in_dtype != FT_F16 && in_dtype != FT_BF16)
+        return FT_ERR_INVALID_ARG;
+    ConvParams p;
+    int64_t planes = 0, tot_out = 0;
+    ft_status st = make_conv_params(input, dims, nd, kernel, kdims, out, p, planes, tot_out);
+    if (st != FT_OK) return st;
+    // fused: the copy engine stages the input in its own type and the kernel widens it
+    if (p.Mr > 1 && p.Kc <= 17) {
+        p.in = nullptr;
+        p.in_t = input;
+        p.in_dtype = in_dtype;
+        p.vec_in = 0;
+        bool used = false;
+        st = in_dtype == FT_U8 ? launch_conv_tma_u8(p, planes, s, &used) : launch_conv_tma_16(p, planes, s, &used);
+        if (st != FT_OK || used) return st;
+    }
+    // otherwise an exact FP32 copy of the input in `scratch`, then the FP32 path
+    if (!scratch) return FT_ERR_WORKSPACE;
+    int64_t n = 1;
+    for (int d = 0; d < nd; ++d) n *= dims[d];
+    const unsigned blocks = (unsigned)std::min<int64_t>(ft::ceil_div(n, kThreads), 152 * 32);
+    switch (in_dtype) {
+    case FT_U8: widen_kernel<<<blocks, kThreads, 0, s>>>(static_cast<const unsigned char *>(input), n, scratch); break;
+    case FT_I16: widen_kernel<<<blocks, kThreads, 0, s>>>(static_cast<const short *>(input), n, scratch); break;
+    case FT_F16: widen_kernel<<<blocks, kThreads, 0, s>>>(static_cast<const __half *>(input), n, scratch); break;
+    default: widen_kernel<<<blocks, kThreads, 0, s>>>(static_cast<const __nv_bfloat16 *>(input), n, scratch); break;
+    }
+    if ((st = ft::check_launch()) != FT_OK) return st;
+    return conv_nd_impl(scratch, dims, nd, kernel, kdims, out, s);
 }
 
 // Separable kernel k = f_0 (x) f_1 (x) ... : one 1-D full convolution per axis, each a

@@ -220,3 +220,53 @@ def test_fastconv_separable_full_size_gaussian_sampled():
     g = got.reshape(-1)[pts].astype(np.float64)
     # the factors carry the rank-1 test's rounding (1e-6 of the largest tap)
     assert np.all(np.abs(g - ref) <= 2e-5 * rabs + 1e-30)
+
+
+_TYPED = [torch.uint8, torch.int16, torch.float16, torch.bfloat16]
+
+
+def _typed_input(shape, dtype, seed):
+    rng = np.random.default_rng(seed)
+    if dtype == torch.uint8:
+        return torch.from_numpy(rng.integers(0, 256, shape).astype(np.uint8))
+    if dtype == torch.int16:
+        return torch.from_numpy(rng.integers(-32768, 32768, shape).astype(np.int16))
+    return torch.from_numpy(rng.standard_normal(shape).astype(np.float32) * 3).to(dtype)
+
+
+@pytest.mark.parametrize("dtype", _TYPED)
+@pytest.mark.parametrize("shape,kshape", [
+    ((45, 640), (7, 5)), ((40, 640), (1, 9)), ((33, 320), (3, 17)), ((37, 531), (5, 5)),
+    ((3, 24, 96), (2, 4, 3)), ((700,), (9,)), ((30, 64), (3, 40)), ((20, 96), (2, 2)),
+])
+def test_fastconv_typed_inputs_match_oracle(dtype, shape, kshape):
+    """uint8 / int16 / float16 / bfloat16 inputs, widened to FP32 exactly: the copy
+    engine path (aligned rows, up to 17 kernel columns) and the converted-copy path
+    (odd widths, rank 1, wide kernels) against the oracle on the same values."""
+    x = _typed_input(shape, dtype, sum(shape))
+    k = scenes.normal_array(kshape, seed=sum(kshape))
+    dev = torch.device("cuda")
+    got = ft.fastconv_nd(x.to(dev), torch.from_numpy(k).to(dev))
+    ft.fastconv_check()
+    E = x.float().numpy().astype(np.float64)
+    ref, rabs = oracle.fastconv_nd(E, k, with_abs=True)
+    err = np.abs(got.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(err <= REL * rabs + 1e-30), float(np.max(err / np.maximum(rabs, 1e-30)))
+
+
+def test_fastconv_typed_paths_and_errors():
+    """An aligned request runs without scratch (fused staging); an unaligned one asks for
+    it; a bad element type is rejected."""
+    L = ft.load()
+    dev = torch.device("cuda")
+    k = torch.from_numpy(scenes.normal_array((5, 5), seed=1)).to(dev)
+    import ctypes
+    dims = (ctypes.c_int64 * 2)(32, 64)
+    kd = (ctypes.c_int64 * 2)(5, 5)
+    x = torch.zeros((32, 64), dtype=torch.uint8, device=dev)
+    out = torch.empty((36, 68), device=dev)
+    assert L.fastconv_nd_typed(x.data_ptr(), 0, dims, 2, k.data_ptr(), kd, out.data_ptr(), None, None) == 0
+    dims2 = (ctypes.c_int64 * 2)(32, 63)
+    assert L.fastconv_nd_typed(x.data_ptr(), 0, dims2, 2, k.data_ptr(), kd, out.data_ptr(), None, None) == 4
+    assert L.fastconv_nd_typed(x.data_ptr(), 9, dims, 2, k.data_ptr(), kd, out.data_ptr(), None, None) == 1
+    torch.cuda.synchronize()
