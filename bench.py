@@ -240,6 +240,36 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
                      "GFLOPps": flops / t / 1e9, "fma_frac": flops / t / fma_peak, "algorithmic_bytes": byts,
                      "flops": flops})
 
+    # direct vs FFT on one 1080 x 1920 image with K x K N(0,1) kernels: where the FFT
+    # path starts to win (the paper's switch, Sec. IV-D)
+    Ec = torch.from_numpy(scenes.uniform_array((1080, 1920), seed=2024)).to(dev)
+    cross = []
+    for K in (9, 15, 21, 25, 31, 41, 51, 63):
+        k = torch.from_numpy(scenes.normal_array((K, K), seed=K)).to(dev)
+        out = ft.fastconv_nd(Ec, k)
+        ws = ft.fastconv_fft(Ec, k, out=torch.empty_like(out))._fastconv_workspace
+        t_dir, t_fft = [], []
+        for i in range(reps + 2):
+            for fn, acc in ((lambda: ft.fastconv_nd(Ec, k, out=out), t_dir),
+                            (lambda: ft.fastconv_fft(Ec, k, out=out, workspace=ws), t_fft)):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                fn()
+                e1.record(s)
+                acc.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        td = float(np.median([a.elapsed_time(b) for a, b in t_dir[2:]])) * 1e3
+        tf = float(np.median([a.elapsed_time(b) for a, b in t_fft[2:]])) * 1e3
+        cross.append({"K": K, "direct_us": td, "fft_us": tf, "faster": "fft" if tf < td else "direct"})
+    import ctypes
+    L = ft.load()
+    auto = [K for K in range(3, 80) if L.fastconv_prefers_fft((ctypes.c_int64 * 2)(1080, 1920), 2,
+                                                              (ctypes.c_int64 * 2)(K, K))]
+    rows.append({"input": [1080, 1920], "crossover_direct_vs_fft": cross,
+                 "library_switches_to_fft_at_K": auto[0] if auto else None})
+
     # separable kernels through one 1-D pass per axis (normalised Gaussians): time and
     # the speedup over the direct path for the same output
     def timed(fn):

@@ -97,6 +97,32 @@ ft_status fastconv_nd_typed(const void *input, int in_dtype, const int64_t *dims
                             const int64_t *kdims, float *out, float *scratch, void *stream);
 
 /*
+ * Full convolution by FFT, for large kernels (Sec. IV-C, IV-D: above a kernel size
+ * threshold the FFT method is faster, and FastConv switches to it).  Ranks 1-3.  Both
+ * operands are zero-padded to FFT extents F_d >= N_d + K_d - 1 (products of 2, 3, 5, 7),
+ * transformed real-to-complex (cuFFT; plans are created on first use of an extent and
+ * cached per device), multiplied pointwise, transformed back and cropped to out.
+ * Error: normwise, about FP32 rounding times log2(prod F) times ||input||_2 ||kernel||_2
+ * per element, unlike the per-element bound of the direct path.
+ *   workspace: device, at least fastconv_fft_workspace() bytes.
+ * Calls from several host threads or streams are serialised on a process-wide lock
+ * while they enqueue the transforms.
+ * Errors: FT_ERR_INVALID_ARG, FT_ERR_SHAPE (as fastconv_nd), FT_ERR_UNSUPPORTED (rank > 3,
+ * more than 2^30 output values), FT_ERR_WORKSPACE, FT_ERR_CUDA (also for cuFFT errors).
+ */
+ft_status fastconv_fft_workspace(const int64_t *dims, int nd, const int64_t *kdims, size_t *bytes);
+ft_status fastconv_fft(const float *input, const int64_t *dims, int nd, const float *kernel, const int64_t *kdims,
+                       float *out, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Host only: 1 when the FFT path is expected to be faster than the direct path for
+ * this request (kernels of at least FT_FFT_MIN_TAPS taps, rank <= 3), 0 otherwise.
+ * FT_FFT_MIN_TAPS is the crossover measured on GB300 for 1080 x 1920 images.
+ */
+#define FT_FFT_MIN_TAPS 1089   /* 33 x 33: direct 116 us at 31 x 31, FFT 125 us, direct 215 us at 41 x 41 */
+int fastconv_prefers_fft(const int64_t *dims, int nd, const int64_t *kdims);
+
+/*
  * Full n-D convolution with a separable kernel k = f_0 (x) f_1 (x) ... (x) f_{nd-1}
  * (outer product of one vector per axis; the paper's Future Work: directional
  * derivatives, Gaussians and block averages are separable): one 1-D full convolution

@@ -20,7 +20,7 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "fastconv_check", "fastconv_separable",
+    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "fastconv_check", "fastconv_separable", "fastconv_fft", "fastconv",
     "factor_kernel", "ttc_derivatives", "gradient",
     "ttc_solve_noalloc",
     "TtcContext", "RESULT_DTYPE", "results_to_numpy", "select_level",
@@ -88,6 +88,12 @@ def load(path: Optional[str] = None):
     L.fastconv_nd.restype = st
     L.fastconv_nd_typed.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_int, _vp, _i64p, _vp, _vp, _vp]
     L.fastconv_nd_typed.restype = st
+    L.fastconv_fft_workspace.argtypes = [_i64p, ctypes.c_int, _i64p, ctypes.POINTER(ctypes.c_size_t)]
+    L.fastconv_fft_workspace.restype = st
+    L.fastconv_fft.argtypes = [_vp, _i64p, ctypes.c_int, _vp, _i64p, _vp, _vp, ctypes.c_size_t, _vp]
+    L.fastconv_fft.restype = st
+    L.fastconv_prefers_fft.argtypes = [_i64p, ctypes.c_int, _i64p]
+    L.fastconv_prefers_fft.restype = ctypes.c_int
     L.fastconv_check.argtypes = [_vp]
     L.fastconv_check.restype = st
     L.fastconv_separable.argtypes = [_vp, _i64p, ctypes.c_int, ctypes.POINTER(_vp), _i64p, _vp, _vp, _vp]
@@ -216,6 +222,44 @@ def fastconv_nd(x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = 
         out._fastconv_scratch = scratch  # alive until the caller drops `out`
     _check(st, "fastconv_nd_typed")
     return out
+
+
+def fastconv_fft(x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = None,
+                 workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Full convolution by FFT (ranks 1-3, float32), for large kernels."""
+    L = load()
+    _require_cuda(x, "x")
+    _require_cuda(k, "k")
+    if x.dtype != torch.float32 or k.dtype != torch.float32 or x.dim() != k.dim():
+        raise ValueError("float32 tensors of one rank")
+    x = x.contiguous()
+    k = k.contiguous()
+    nbytes = ctypes.c_size_t(0)
+    _check(L.fastconv_fft_workspace(_dims(x.shape), x.dim(), _dims(k.shape), ctypes.byref(nbytes)),
+           "fastconv_fft_workspace")
+    if workspace is None or workspace.numel() * workspace.element_size() < nbytes.value:
+        workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=x.device)
+    od = fastconv_out_dims(x.shape, k.shape)
+    out = torch.empty(od, dtype=torch.float32, device=x.device) if out is None else out
+    _check(L.fastconv_fft(x.data_ptr(), _dims(x.shape), x.dim(), k.data_ptr(), _dims(k.shape), out.data_ptr(),
+                          workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(x)),
+           "fastconv_fft")
+    out._fastconv_workspace = workspace
+    return out
+
+
+def fastconv(x: torch.Tensor, k: torch.Tensor, method: str = "auto") -> torch.Tensor:
+    """FastConv with the paper's switch: the direct path, or the FFT path for kernels at
+    or above the measured crossover (method "auto"); "direct" or "fft" force one."""
+    L = load()
+    if method == "auto":
+        use_fft = x.dtype == torch.float32 and bool(L.fastconv_prefers_fft(_dims(x.shape), x.dim(), _dims(k.shape)))
+        method = "fft" if use_fft else "direct"
+    if method == "fft":
+        return fastconv_fft(x, k)
+    if method == "direct":
+        return fastconv_nd(x, k)
+    raise ValueError("method is auto, direct or fft")
 
 
 def fastconv_separable(x: torch.Tensor, factors, out: Optional[torch.Tensor] = None,

@@ -71,7 +71,9 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
         list(ex.map(run, cmds))
     tmp = LIB + f".{os.getpid()}.tmp"
-    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"])
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lcufft", "-L" + cuda_lib,
+         "-Xlinker", "-rpath=" + cuda_lib, "-lrt", "-ldl", "-lpthread"])
     os.replace(tmp, LIB)
     for o in objs:
         os.remove(o)

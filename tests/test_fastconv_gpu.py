@@ -270,3 +270,49 @@ def test_fastconv_typed_paths_and_errors():
     assert L.fastconv_nd_typed(x.data_ptr(), 0, dims2, 2, k.data_ptr(), kd, out.data_ptr(), None, None) == 4
     assert L.fastconv_nd_typed(x.data_ptr(), 9, dims, 2, k.data_ptr(), kd, out.data_ptr(), None, None) == 1
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("shape,kshape", [
+    ((300,), (41,)), ((64, 80), (31, 33)), ((5, 33, 40), (3, 9, 9)), ((7, 9), (12, 30)), ((120, 200), (45, 45)),
+])
+def test_fastconv_fft_matches_oracle_normwise(shape, kshape):
+    """The FFT path against the oracle within its normwise bound: FP32 rounding times
+    log2 of the transform size times ||E||_2 ||k||_2 (a factor 8 of margin)."""
+    E = scenes.uniform_array(shape, seed=sum(shape))
+    k = scenes.normal_array(kshape, seed=sum(kshape))
+    dev = torch.device("cuda")
+    got = ft.fastconv_fft(torch.from_numpy(E).to(dev), torch.from_numpy(k).to(dev)).cpu().numpy()
+    ref = oracle.fastconv_nd(E, k)
+    R = np.prod([m + 8 for m in ref.shape])
+    bound = 8 * 2.0 ** -24 * np.log2(R) * np.linalg.norm(E.ravel()) * np.linalg.norm(k.ravel())
+    err = np.abs(got.astype(np.float64) - ref)
+    assert err.max() <= bound, (err.max(), bound)
+
+
+def test_fastconv_fft_errors_and_auto_switch():
+    L = ft.load()
+    import ctypes
+    dims = (ctypes.c_int64 * 4)(2, 2, 8, 8)
+    kd = (ctypes.c_int64 * 4)(1, 1, 3, 3)
+    b = ctypes.c_size_t()
+    assert L.fastconv_fft_workspace(dims, 4, kd, ctypes.byref(b)) == 3          # rank 4
+    dev = torch.device("cuda")
+    x = torch.rand((64, 64), device=dev)
+    k = torch.rand((5, 5), device=dev)
+    with pytest.raises(ft.FtError):
+        _fft_small_workspace(L, x, k)                                    # workspace too small
+    small = ft.fastconv(x, k)                                   # below the threshold: direct
+    big = ft.fastconv(x, torch.rand((41, 41), device=dev))      # at or above: FFT
+    assert small.shape == (68, 68) and big.shape == (104, 104)
+    assert L.fastconv_prefers_fft((ctypes.c_int64 * 2)(64, 64), 2, (ctypes.c_int64 * 2)(31, 31)) == 0
+    assert L.fastconv_prefers_fft((ctypes.c_int64 * 2)(64, 64), 2, (ctypes.c_int64 * 2)(33, 33)) == 1
+
+
+def _fft_small_workspace(L, x, k):
+    import ctypes
+    out = torch.empty((68, 68), device=x.device)
+    ws = torch.empty(16, dtype=torch.uint8, device=x.device)
+    st = L.fastconv_fft(x.data_ptr(), (ctypes.c_int64 * 2)(64, 64), 2, k.data_ptr(), (ctypes.c_int64 * 2)(5, 5),
+                        out.data_ptr(), ws.data_ptr(), 16, None)
+    if st != 0:
+        raise ft.FtError(st, "fastconv_fft")
