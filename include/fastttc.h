@@ -158,6 +158,16 @@ int fastconv_factor(const float *kernel, const int64_t *kdims, int nd, double re
  */
 ft_status fastconv_check(void *stream);
 
+/*
+ * Test switch for the timeout paths (no counterpart in the paper).  While on (nonzero),
+ * kernels that wait for copy-engine transfers and are launched afterwards expect 16
+ * more bytes than their copies deliver: every copy still lands, but each bounded wait
+ * gives up after about 2 s of GPU clock, the kernel reports it (FT_FLAG_TIMEOUT in the
+ * TTC records, FT_ERR_TIMEOUT from fastconv_check) and returns; results of those calls
+ * are incomplete.  Off (0) restores normal operation.  Process-wide; not for production.
+ */
+void ft_test_stall_tma_waits(int on);
+
 /* ------------------------------------------------------------------------ */
 /* Time to contact (Sec. V-A, V-B)                                           */
 /* ------------------------------------------------------------------------ */

@@ -31,6 +31,7 @@ __all__ = [
 MODE_TTC, MODE_FOE = 0, 1
 DTYPE_U8, DTYPE_F32 = 0, 1
 FLAG_SINGULAR, FLAG_C_ZERO, FLAG_RECEDING, FLAG_TIMEOUT = 1, 2, 4, 8
+ERR_TIMEOUT = 6
 MAX_LEVELS = 7
 MAX_NDIM = 8
 
@@ -94,6 +95,8 @@ def load(path: Optional[str] = None):
     L.fastconv_fft.restype = st
     L.fastconv_prefers_fft.argtypes = [_i64p, ctypes.c_int, _i64p]
     L.fastconv_prefers_fft.restype = ctypes.c_int
+    L.ft_test_stall_tma_waits.argtypes = [ctypes.c_int]
+    L.ft_test_stall_tma_waits.restype = None
     L.fastconv_check.argtypes = [_vp]
     L.fastconv_check.restype = st
     L.fastconv_separable.argtypes = [_vp, _i64p, ctypes.c_int, ctypes.POINTER(_vp), _i64p, _vp, _vp, _vp]

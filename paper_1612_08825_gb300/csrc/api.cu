@@ -1,4 +1,5 @@
 // Status strings, version and CUDA-error bookkeeping of the fastttc C ABI.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -15,6 +16,12 @@ void set_cuda_error(cudaError_t e)
     std::strncpy(g_cuda_error, s ? s : "unknown CUDA error", sizeof(g_cuda_error) - 1);
     g_cuda_error[sizeof(g_cuda_error) - 1] = '\0';
 }
+
+static std::atomic<unsigned> g_tma_extra_tx{0};
+
+unsigned tma_extra_tx() { return g_tma_extra_tx.load(); }
+
+void set_tma_extra_tx(unsigned v) { g_tma_extra_tx.store(v); }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
@@ -51,3 +58,5 @@ extern "C" const char *ft_status_string(int status)
 extern "C" const char *ft_last_cuda_error(void) { return ft::g_cuda_error; }
 
 extern "C" int ft_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+extern "C" void ft_test_stall_tma_waits(int on) { ft::set_tma_extra_tx(on ? 16u : 0u); }

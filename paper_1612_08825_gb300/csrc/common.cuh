@@ -11,6 +11,9 @@ namespace ft {
 // Records the text of a CUDA error for ft_last_cuda_error() (thread-local).
 void set_cuda_error(cudaError_t e);
 
+// the byte count TMA-fed kernels add to their barriers' expected bytes (test switch)
+void set_tma_extra_tx(unsigned v);
+
 // FT_OK if the last launch on this thread succeeded, else FT_ERR_CUDA.
 inline ft_status check_launch()
 {

@@ -95,6 +95,7 @@ struct Params {
     int buf_bytes;               // bytes per staging buffer (whole 128-byte units)
     int store_tma;               // 1: output tiles leave by TMA store, 0: by plain stores
     int *status;                 // set to 1 when a wait gives up
+    unsigned extra_tx;           // added to the expected bytes (0; tests of the timeout path)
 };
 
 // work items: (plane, tile, R) with tile t of output plane `plane` (the CTA's tiles are
@@ -131,7 +132,7 @@ __device__ __forceinline__ void issue(const CUtensorMap *m, const Params &cp, co
 {
     const int ty = it.tile / cp.tiles_x, tx = it.tile - ty * cp.tiles_x;
     ft_tma::fence_proxy_async();
-    ft_tma::mbar_expect_tx(bar, (uint32_t)(cp.SH * (TW + PADT) * (int)sizeof(T)));
+    ft_tma::mbar_expect_tx(bar, (uint32_t)(cp.SH * (TW + PADT) * (int)sizeof(T)) + cp.extra_tx);
     ft_tma::tma_load_3d(buf, m, tx * TW - PADT, ty * TH - ((int)cp.p.Kr - 1), (int)it.q, bar);
 }
 
@@ -370,6 +371,7 @@ ft_status launch_tma(const ConvParams &p, int64_t planes, cudaStream_t s, bool *
     }
     if (per_sm < 1) return FT_OK;
     cp.status = st;
+    cp.extra_tx = ft::tma_extra_tx();
     const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)per_sm * nsm);
     conv_tma_kernel<T, NTAP, SMALLR><<<(unsigned)grid, kThreads, smem, s>>>(in_map, out_map, cp);
     *used = true;

@@ -85,4 +85,9 @@ namespace ft {
 // cuTensorMapEncodeTiled from the driver (null when unavailable)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
+// Bytes that TMA-fed kernels launched from now on add to the byte count their barriers
+// expect (0 normally; set by ft_test_stall_tma_waits so that tests can make the
+// bounded waits run out without any fault).
+unsigned tma_extra_tx();
+
 }  // namespace ft

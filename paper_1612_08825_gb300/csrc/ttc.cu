@@ -519,6 +519,7 @@ bool launch_level0_tma(const ttc_pass::PassParams &p, const void *prev, const vo
     tp.p = p;
     tp.total = npairs * p.ntiles;
     tp.status = status;
+    tp.extra_tx = ft::tma_extra_tx();
     const int grid = std::min(tp.total, 2 * std::max(nsm, 1));
     if (p.next) {
         *err = cudaFuncSetAttribute(ttc_tma::ttc_pass_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -36,6 +36,7 @@ struct TmaParams {
     PassParams p;               // geometry, partials, next level (prev/cur unused)
     int total;                  // npairs * ntiles
     int *status;                // set to 1 when a wait gives up
+    unsigned extra_tx;          // added to the expected bytes (0; tests of the timeout path)
 };
 
 using namespace ft_tma;
@@ -51,7 +52,7 @@ __device__ __forceinline__ void issue_tile(const TmaParams &tp, const CUtensorMa
     const int R0 = ty * TR, C0 = tx * TC;
     // generic-proxy reads of this buffer (previous tile) are ordered before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, TX);
+    mbar_expect_tx(bar, TX + tp.extra_tx);
     tma_load_3d(buf, ma, C0, R0, pair, bar);
     tma_load_3d(buf + BOX, ma, C0 + BW, R0, pair, bar);
     tma_load_3d(buf + 2 * BOX, xa, C0 + 2 * BW, R0, pair, bar);
