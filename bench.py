@@ -420,8 +420,8 @@ def serve_bench(dev, args):
     both saturated; plus admission under a small HBM budget."""
     import torch
     import scenes
-    from paper_1612_08825_gb300.serve import (CudaBatchEngine, PerFrameEngine, Server, latency_summary, replay,
-                                              saturate)
+    from paper_1612_08825_gb300.serve import (CudaBatchEngine, NativeServer, PerFrameEngine, Server,
+                                              latency_summary, replay, saturate)
     levels, K = 4, 4
     specs = scenes.camera_streams(16, seed=args.seed)
     frames = {}
@@ -437,14 +437,20 @@ def serve_bench(dev, args):
                        "Poisson arrivals, 30 fps per stream; 4 levels; FOE",
            "offered_pairs_per_s": len(arr) / args.serve_seconds}
     rows = None
-    for kind in ("batch", "per_frame"):
+    for kind in ("native", "batch", "per_frame"):
         if kind == "batch":
             eng = CudaBatchEngine(1080, 1920, levels, max_batch=len(specs), device=dev)
-            rows = eng.autotune([(frames[s][0], frames[s][1]) for s, *_ in specs])
             srv = Server(eng, 40 << 30, max_batch=len(specs))
+        elif kind == "native":
+            tuner = CudaBatchEngine(1080, 1920, levels, max_batch=len(specs), device=dev)
+            rows = tuner.autotune([(frames[s][0], frames[s][1]) for s, *_ in specs])
+            del tuner
+            eng = srv = NativeServer(1080, 1920, levels, 40 << 30, max_batch=len(specs), rows_per_tile=rows)
         else:
             eng = PerFrameEngine(1080, 1920, levels, device=dev)
             srv = Server(eng, 40 << 30, max_batch=1)
+        if kind == "batch":
+            eng.set_plan(rows)
         for sid, H, W, *_ in specs:
             assert srv.admit(sid, H, W)
         saturate(srv, fn, ticks=3 if kind == "batch" else 3 * len(specs))      # warm-up
@@ -457,21 +463,26 @@ def serve_bench(dev, args):
         res.update({"served_pairs_per_s": res["n"] / dt, "ticks": ticks,
                     "mean_pairs_per_tick": res["n"] / max(ticks, 1),
                     "dropped_frames": srv.stats["dropped_frames"] - base.get("dropped_frames", 0)})
-        nt = 100 if kind == "batch" else 100 * len(specs) // 8
-        l0 = eng.launches
+        nt = 100 * len(specs) // 8 if kind == "per_frame" else 100
+        l0 = getattr(eng, "launches", 0)
         t0 = time.perf_counter()
         sat = saturate(srv, fn, ticks=nt)
         dt = time.perf_counter() - t0
         npairs = sum(1 for c in sat if c.records is not None)
         res["saturated_pairs_per_s"] = npairs / dt
-        res["saturated_launches_per_pair"] = (eng.launches - l0) / max(npairs, 1)
-        if kind == "batch":
+        if kind != "native":
+            res["saturated_launches_per_pair"] = (eng.launches - l0) / max(npairs, 1)
+        if kind != "per_frame":
             res["rows_per_tile_per_level"] = rows
             res["hbm_bytes_admitted"] = srv.used
         out[kind] = res
+        if kind == "native":
+            srv.close()
         del srv, eng
         torch.cuda.synchronize(dev)
     out["batch_vs_per_frame_saturated"] = out["batch"]["saturated_pairs_per_s"] / out["per_frame"]["saturated_pairs_per_s"]
+    out["native_vs_per_frame_saturated"] = (out["native"]["saturated_pairs_per_s"] /
+                                            out["per_frame"]["saturated_pairs_per_s"])
     # admission under a small budget: fixed workspace plus room for about 20 streams
     eng = CudaBatchEngine(1080, 1920, levels, max_batch=len(specs), device=dev)
     per = [eng.stream_bytes(H, W) for _, H, W, *_ in specs]

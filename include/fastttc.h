@@ -408,6 +408,69 @@ ft_status ttc_pyramid_layout(int H, int W, int levels, int dtype, int64_t *offse
 ft_status ttc_batch_set_plan(ttc_ctx *ctx, const int *rows_per_tile, int levels);
 
 /*
+ * Serving runtime (no counterpart in the paper, which processes one camera): many
+ * camera streams with continuous batching over ttc_batch_prepare / ttc_batch_run.
+ * Each admitted stream owns three device frame slots and two pyramid blocks (its last
+ * two frames' levels 1..L-1; see ttc_pyramid_layout), so each frame is uploaded once
+ * and its pyramid built once.  ttc_server_step launches a tick when fewer than two are
+ * in flight: at most one waiting frame per stream (oldest arrival first, at most
+ * max_batch pairs), uploaded from the caller's host memory on the server's copy stream
+ * (one 2-D copy per frame), then one batch on the server's compute stream with the
+ * records copied to page-locked host memory; it also reports every frame whose fate is
+ * settled.  The multi-scale rule (Sec. V-B) picks each result's level on the host.
+ *   ttc_server_create: dtype FT_U8 or FT_F32 frames; levels, mode, rule as elsewhere;
+ *     max_batch pairs per tick; max_streams open streams; max_pending waiting frames per
+ *     stream (a new frame beyond that drops the oldest); hbm_budget_bytes bounds the
+ *     server's device memory (context, result buffers and every stream's buffers);
+ *     rows_per_tile: host, levels entries (16 or 64), nullable (64 everywhere): the
+ *     fixed tile plan, so a stream's records do not depend on the other streams.
+ *   ttc_server_admit: a stream of H x W frames; FT_ERR_WORKSPACE when the budget, the
+ *     stream count or the server's maximum frame size would be exceeded.
+ *   ttc_server_submit: a frame (host, H rows of W pixels, row stride pitch_bytes; page-
+ *     locked memory for asynchronous uploads) that must stay valid and unchanged until
+ *     its report; seq and t_arrival are returned in the report unchanged.
+ *   ttc_server_remove: the stream goes away; its waiting frames are reported dropped, its
+ *     frames in flight discarded, its buffers freed once no tick in flight uses them.  A
+ *     stream's first frame (after admission) has no result.
+ *   ttc_server_step: wait != 0 blocks until at least one report is ready when a tick is
+ *     in flight; writes up to max_done reports (host) and their count.
+ * Errors: FT_ERR_INVALID_ARG (null, bad id or enum), FT_ERR_SHAPE (pitch), FT_ERR_WORKSPACE,
+ * FT_ERR_CUDA.  A server is driven from one host thread.
+ */
+typedef enum {
+    FT_SERVED_RESULT = 1,       /* records[0..levels-1] and level are valid */
+    FT_SERVED_FIRST_FRAME = 0,  /* the stream's first frame: it only became the resident frame */
+    FT_SERVED_DROPPED = -1,     /* never processed (queue overflow or stream removed) */
+    FT_SERVED_DISCARDED = -2    /* processed, but its stream was removed meanwhile */
+} ft_served_status;
+typedef struct {
+    ttc_level_result records[FT_MAX_LEVELS];
+    double t_arrival;
+    int64_t seq;
+    int stream;
+    int status;                 /* ft_served_status */
+    int level;                  /* chosen level, -1 when none */
+    int pad;
+} ttc_served;
+typedef struct ttc_server ttc_server;
+ft_status ttc_server_create(ttc_server **srv, int max_H, int max_W, int levels, int mode, int rule, int dtype,
+                            int max_batch, int max_streams, int max_pending, int64_t hbm_budget_bytes,
+                            const int *rows_per_tile);
+void ttc_server_destroy(ttc_server *srv);
+ft_status ttc_server_stream_bytes(const ttc_server *srv, int H, int W, int64_t *bytes);
+ft_status ttc_server_admit(ttc_server *srv, int H, int W, int *stream_id);
+ft_status ttc_server_remove(ttc_server *srv, int stream_id);
+ft_status ttc_server_submit(ttc_server *srv, int stream_id, const void *frame, int64_t pitch_bytes, int64_t seq,
+                            double t_arrival);
+ft_status ttc_server_step(ttc_server *srv, int wait, ttc_served *done, int max_done, int *n_done);
+int ttc_server_in_flight(const ttc_server *srv);        /* ticks in flight */
+int64_t ttc_server_ticks(const ttc_server *srv);        /* ticks launched so far */
+int ttc_server_waiting(const ttc_server *srv, int stream_id);   /* the stream's waiting frames; all waiting
+                                                                   frames and unreturned reports if < 0 */
+int64_t ttc_server_bytes_in_use(const ttc_server *srv);
+int ttc_server_launches(const ttc_server *srv);         /* kernels of the last batch run */
+
+/*
  * Timing hook (no counterpart in the paper): when start and end are non-null
  * (cudaEvent_t values passed as void*), every later ttc_partial_sums /
  * ttc_solve_sequence / ttc_solve on this context records `start` on its stream just

@@ -46,6 +46,14 @@ RESULT_DTYPE = np.dtype([
 ])
 assert RESULT_DTYPE.itemsize == 152
 
+# mirror of ttc_served (one report of the serving runtime)
+SERVED_DTYPE = np.dtype([
+    ("records", RESULT_DTYPE, (7,)),
+    ("t_arrival", np.float64), ("seq", np.int64),
+    ("stream", np.int32), ("status", np.int32), ("level", np.int32), ("pad", np.int32),
+])
+assert SERVED_DTYPE.itemsize == 1096
+
 _lib = None
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _vp = ctypes.c_void_p
@@ -145,6 +153,32 @@ def load(path: Optional[str] = None):
     L.ttc_pyramid_layout.restype = st
     L.ttc_batch_set_plan.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     L.ttc_batch_set_plan.restype = st
+    L.ttc_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
+    L.ttc_server_create.restype = st
+    L.ttc_server_destroy.argtypes = [_vp]
+    L.ttc_server_destroy.restype = None
+    L.ttc_server_stream_bytes.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _i64p]
+    L.ttc_server_stream_bytes.restype = st
+    L.ttc_server_admit.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.ttc_server_admit.restype = st
+    L.ttc_server_remove.argtypes = [_vp, ctypes.c_int]
+    L.ttc_server_remove.restype = st
+    L.ttc_server_submit.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double]
+    L.ttc_server_submit.restype = st
+    L.ttc_server_step.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.ttc_server_step.restype = st
+    L.ttc_server_in_flight.argtypes = [_vp]
+    L.ttc_server_in_flight.restype = ctypes.c_int
+    L.ttc_server_ticks.argtypes = [_vp]
+    L.ttc_server_ticks.restype = ctypes.c_int64
+    L.ttc_server_waiting.argtypes = [_vp, ctypes.c_int]
+    L.ttc_server_waiting.restype = ctypes.c_int
+    L.ttc_server_bytes_in_use.argtypes = [_vp]
+    L.ttc_server_bytes_in_use.restype = ctypes.c_int64
+    L.ttc_server_launches.argtypes = [_vp]
+    L.ttc_server_launches.restype = ctypes.c_int
     L.ttc_select_level.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.ttc_select_level.restype = ctypes.c_int
     _lib = L

@@ -35,7 +35,8 @@ import torch
 from . import (MODE_FOE, RESULT_DTYPE, TtcContext, _frame_args, pyramid_layout, results_to_numpy,
                select_level)
 
-__all__ = ["Frame", "Completed", "Server", "CudaBatchEngine", "PerFrameEngine", "latency_summary"]
+__all__ = ["Frame", "Completed", "Server", "NativeServer", "CudaBatchEngine", "PerFrameEngine", "latency_summary",
+           "replay", "saturate"]
 
 
 @dataclasses.dataclass
@@ -446,7 +447,136 @@ def saturate(server: Server, frame_fn, ticks: int, clock=time.perf_counter) -> L
                     server.offer(Frame(sid, seq[sid], clock(), frame_fn(sid, seq[sid])))
                     seq[sid] += 1
         done += server.step(block=len(server.ticks) >= server.max_in_flight)
-    for st in server.streams.values():
-        server.stats["left_pending"] += len(st.pending)
-        st.pending.clear()
+    # frames still waiting when the target was reached went into further ticks: the loop
+    # ends only when nothing is in flight, and a step launches whatever waits
     return done
+
+
+class _NativeStream:
+    def __init__(self, srv, nid, H, W):
+        self._srv, self.nid, self.H, self.W = srv, nid, H, W
+        self.closed = False
+
+    @property
+    def pending(self):
+        # waiting frames (not yet in a tick), as the drivers expect
+        return self._srv._L.ttc_server_waiting(self._srv._h, self.nid)
+
+
+class NativeServer:
+    """The serving runtime of the library (ttc_server_*): the same admission, ticks and
+    fault handling as Server, run natively (uploads, batch, records, level choice), with
+    the interface the replay / saturate drivers use."""
+
+    def __init__(self, max_H: int, max_W: int, levels: int, hbm_budget_bytes: int, max_batch: int,
+                 mode: int = MODE_FOE, rule: int = 0, dtype=torch.uint8, max_streams: int = 256,
+                 max_pending: int = 4, rows_per_tile: Optional[list] = None, clock=time.perf_counter):
+        import ctypes
+        from . import SERVED_DTYPE, load, _check, _vp
+        self._ct = ctypes
+        self._L = load()
+        self._SERVED = SERVED_DTYPE
+        self.levels, self.rule, self.dtype = levels, rule, dtype
+        self.max_in_flight = 2
+        self.clock = clock
+        rows = (ctypes.c_int * levels)(*(rows_per_tile or [64] * levels))
+        h = _vp()
+        _check(self._L.ttc_server_create(ctypes.byref(h), max_H, max_W, levels, mode, rule,
+                                         0 if dtype == torch.uint8 else 1, max_batch, max_streams, max_pending,
+                                         int(hbm_budget_bytes), rows), "ttc_server_create")
+        self._h = h
+        self._check = _check
+        self.streams: Dict[int, _NativeStream] = {}
+        self._keep: Dict[tuple, Frame] = {}
+        self._buf = np.zeros(256, dtype=SERVED_DTYPE)
+        self.stats = collections.Counter()
+
+    @property
+    def used(self) -> int:
+        return int(self._L.ttc_server_bytes_in_use(self._h))
+
+    @property
+    def ticks(self):
+        return [None] * int(self._L.ttc_server_in_flight(self._h))
+
+    def pending_frames(self) -> int:
+        return int(self._L.ttc_server_waiting(self._h, -1))
+
+    def admit(self, sid: int, H: int, W: int) -> bool:
+        if sid in self.streams:
+            raise ValueError(f"stream {sid} is already admitted")
+        nid = self._ct.c_int(-1)
+        st = self._L.ttc_server_admit(self._h, H, W, self._ct.byref(nid))
+        if st == 4:
+            self.stats["rejected_streams"] += 1
+            return False
+        self._check(st, "ttc_server_admit")
+        self.streams[sid] = _NativeStream(self, nid.value, H, W)
+        self._sid = getattr(self, "_sid", {})
+        self._sid[nid.value] = sid
+        self.stats["admitted_streams"] += 1
+        return True
+
+    def remove(self, sid: int):
+        st = self.streams.pop(sid, None)
+        if st is None:
+            return
+        st.closed = True
+        self._check(self._L.ttc_server_remove(self._h, st.nid), "ttc_server_remove")
+
+    def offer(self, frame: Frame) -> bool:
+        st = self.streams.get(frame.stream)
+        d = frame.data
+        if (st is None or not isinstance(d, torch.Tensor) or d.dim() != 2 or d.is_cuda or d.dtype != self.dtype
+                or tuple(d.shape) != (st.H, st.W) or d.stride(1) != 1):
+            self.stats["rejected_frames"] += 1
+            return False
+        r = self._L.ttc_server_submit(self._h, st.nid, d.data_ptr(), d.stride(0) * d.element_size(),
+                                      int(frame.seq), float(frame.t_arrival))
+        if r != 0:
+            self.stats["rejected_frames"] += 1
+            return False
+        self._keep[(st.nid, int(frame.seq))] = frame      # alive until reported
+        self.stats["offered_frames"] += 1
+        return True
+
+    def step(self, block: bool = False) -> List[Completed]:
+        n = self._ct.c_int(0)
+        self._check(self._L.ttc_server_step(self._h, 1 if block else 0, self._buf.ctypes.data, len(self._buf),
+                                            self._ct.byref(n)), "ttc_server_step")
+        t_done = self.clock()
+        out = []
+        for r in self._buf[:n.value]:
+            nid, seq, status = int(r["stream"]), int(r["seq"]), int(r["status"])
+            self._keep.pop((nid, seq), None)
+            sid = self._sid.get(nid, nid)
+            if status == 1:
+                out.append(Completed(sid, seq, float(r["t_arrival"]), t_done, r["records"][:self.levels].copy(),
+                                     int(r["level"])))
+                self.stats["results"] += 1
+            elif status == 0:
+                out.append(Completed(sid, seq, float(r["t_arrival"]), t_done, None, -1))
+                self.stats["first_frames"] += 1
+            elif status == -1:
+                self.stats["dropped_frames"] += 1
+            else:
+                self.stats["discarded_results"] += 1
+        self.stats["ticks"] = int(self._L.ttc_server_ticks(self._h))
+        return out
+
+    def drain(self) -> List[Completed]:
+        out = []
+        while self.ticks or self.pending_frames():
+            out += self.step(block=True)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.ttc_server_destroy(self._h)
+            self._h = self._ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -181,3 +181,79 @@ def test_replay_and_saturate_on_gpu():
     saturate(srv, lambda s, q: frames[s][q % 3], ticks=6)
     assert srv.stats["results"] - n0 >= 5 * len(STREAMS)
     assert eng.launches > 0
+
+
+from paper_1612_08825_gb300.serve import NativeServer  # noqa: E402
+
+
+def _serve_native(streams, frames, remove_at=None, max_pending=4):
+    srv = NativeServer(1080, 1920, LEVELS, 40 << 30, max_batch=8, rows_per_tile=PLAN, max_pending=max_pending)
+    for sid, H, W in streams:
+        assert srv.admit(sid, H, W)
+    done = []
+    for k in range(NFR):
+        for sid, _, _ in streams:
+            if remove_at is not None and (sid, k) == remove_at:
+                srv.remove(sid)
+            srv.offer(Frame(sid, k, float(k), frames[sid][k]))
+        done += srv.step()
+    done += srv.drain()
+    return done, srv
+
+
+def test_native_server_matches_python_server_bitwise():
+    """The native serving runtime and the Python server over the same batch API give
+    bitwise the same records and level choices for every frame."""
+    frames = {sid: _video(H, W, NFR, 900 + sid).pin_memory() for sid, H, W in STREAMS}
+    py, _ = _serve(STREAMS, frames)
+    nat, srv = _serve_native(STREAMS, frames)
+    assert srv.stats["results"] == len(STREAMS) * (NFR - 1) and srv.stats["first_frames"] == len(STREAMS)
+    a = {(c.stream, c.seq): c for c in py}
+    b = {(c.stream, c.seq): c for c in nat}
+    assert a.keys() == b.keys()
+    for key, c in a.items():
+        if c.records is None:
+            assert b[key].records is None
+        else:
+            assert b[key].records.tobytes() == c.records.tobytes(), key
+            assert b[key].level == c.level
+    srv.close()
+
+
+def test_native_server_faults():
+    frames = {sid: _video(H, W, NFR, 950 + sid).pin_memory() for sid, H, W in STREAMS}
+    cut, srv = _serve_native(STREAMS, frames, remove_at=(3, 2))
+    assert all(c.stream != 3 or c.seq < 2 for c in cut)
+    full = {(c.stream, c.seq): c.records for c in _serve_native(STREAMS, frames)[0]}
+    for c in cut:
+        if c.records is not None:
+            assert c.records.tobytes() == full[(c.stream, c.seq)].tobytes()
+    srv.close()
+    # queue overflow: five frames offered before any step with room for two
+    srv = NativeServer(480, 640, LEVELS, 40 << 30, max_batch=8, rows_per_tile=PLAN, max_pending=2)
+    assert srv.admit(0, 480, 640)
+    f = _video(480, 640, 5, 77).pin_memory()
+    for k in range(5):
+        assert srv.offer(Frame(0, k, float(k), f[k]))
+    done = srv.drain()
+    assert srv.stats["dropped_frames"] == 3 and [c.seq for c in done] == [3, 4]
+    # malformed and oversized requests
+    assert not srv.offer(Frame(0, 9, 0.0, f[0][:, :100]))
+    assert not srv.admit(1, 1080, 1920)                        # larger than the server's frames
+    srv.close()
+    with pytest.raises(ft.FtError):
+        NativeServer(480, 640, LEVELS, 1024, max_batch=8)     # the budget cannot hold the workspace
+
+
+def test_native_server_replay_and_saturate():
+    frames = {sid: _video(H, W, 3, 990 + sid).pin_memory() for sid, H, W in STREAMS}
+    srv = NativeServer(1080, 1920, LEVELS, 40 << 30, max_batch=8, rows_per_tile=PLAN)
+    for sid, H, W in STREAMS:
+        srv.admit(sid, H, W)
+    arr = scenes.poisson_arrivals(len(STREAMS), 200.0, 0.05, seed=3)
+    done = replay(srv, arr, lambda s, q: frames[s][q % 3])
+    assert len(done) == len(arr) - srv.stats["dropped_frames"]
+    n0 = srv.stats["results"]
+    saturate(srv, lambda s, q: frames[s][q % 3], ticks=6)
+    assert srv.stats["results"] - n0 >= 5 * len(STREAMS)
+    srv.close()
