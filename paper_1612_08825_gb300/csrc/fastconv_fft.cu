@@ -8,6 +8,8 @@
 // are this file's kernels; the transforms are cuFFT's, with plans cached per shape.
 #include <cufft.h>
 
+#include <algorithm>
+
 #include <map>
 #include <mutex>
 #include <vector>
@@ -87,17 +89,20 @@ struct Ext {
     int64_t a[3];           // extents, last fastest, unused leading ones 1
 };
 
-// dst (F extents, all R values) = src (N extents) zero-padded at the high end
-__global__ void __launch_bounds__(kThreads) pad_kernel(const float *__restrict__ src, Ext N, Ext F, int64_t R,
+// dst (F extents, all R values) = src (N extents) zero-padded at the high end: block
+// row blockIdx.y of the grid is destination row r = z * F1 + y, threads stride its
+// columns (no divisions per element)
+__global__ void __launch_bounds__(kThreads) pad_kernel(const float *__restrict__ src, Ext N, Ext F,
                                                        float *__restrict__ dst)
 {
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < R; i += (int64_t)gridDim.x * kThreads) {
-        const int64_t x = i % F.a[2], r = i / F.a[2];
-        const int64_t y = r % F.a[1], z = r / F.a[1];
-        float v = 0.f;
-        if (x < N.a[2] && y < N.a[1] && z < N.a[0]) v = __ldg(src + (z * N.a[1] + y) * N.a[2] + x);
-        dst[i] = v;
-    }
+    const int64_t r = blockIdx.y + (int64_t)blockIdx.z * gridDim.y;
+    if (r >= F.a[0] * F.a[1]) return;
+    const int64_t z = r / F.a[1], y = r - z * F.a[1];
+    const bool row_in = z < N.a[0] && y < N.a[1];
+    const float *s = src + (z * N.a[1] + y) * N.a[2];
+    float *d = dst + r * F.a[2];
+    for (int64_t x = blockIdx.x * (int64_t)kThreads + threadIdx.x; x < F.a[2]; x += (int64_t)gridDim.x * kThreads)
+        d[x] = (row_in && x < N.a[2]) ? __ldg(s + x) : 0.f;
 }
 
 // a[i] = a[i] * b[i] * scale
@@ -110,15 +115,17 @@ __global__ void __launch_bounds__(kThreads) mul_kernel(cufftComplex *__restrict_
     }
 }
 
-// out (M extents) = the M corner of src (F extents)
-__global__ void __launch_bounds__(kThreads) crop_kernel(const float *__restrict__ src, Ext F, Ext M, int64_t n,
+// out (M extents) = the M corner of src (F extents), one block row per output row
+__global__ void __launch_bounds__(kThreads) crop_kernel(const float *__restrict__ src, Ext F, Ext M,
                                                         float *__restrict__ out)
 {
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        const int64_t x = i % M.a[2], r = i / M.a[2];
-        const int64_t y = r % M.a[1], z = r / M.a[1];
-        out[i] = src[(z * F.a[1] + y) * F.a[2] + x];
-    }
+    const int64_t r = blockIdx.y + (int64_t)blockIdx.z * gridDim.y;
+    if (r >= M.a[0] * M.a[1]) return;
+    const int64_t z = r / M.a[1], y = r - z * M.a[1];
+    const float *s = src + (z * F.a[1] + y) * F.a[2];
+    float *o = out + r * M.a[2];
+    for (int64_t x = blockIdx.x * (int64_t)kThreads + threadIdx.x; x < M.a[2]; x += (int64_t)gridDim.x * kThreads)
+        o[x] = s[x];
 }
 
 Ext ext3(const int64_t *v, int nd)
@@ -132,6 +139,15 @@ unsigned grid_for(int64_t n)
 {
     const int64_t b = ft::ceil_div(n, kThreads);
     return (unsigned)(b < 152 * 16 ? b : 152 * 16);
+}
+
+// grid for a row kernel: x over the columns (at most 8 blocks), y * z over the rows
+dim3 row_grid(int64_t rows, int64_t cols)
+{
+    const int64_t bx = std::min<int64_t>(ft::ceil_div(cols, kThreads), 8);
+    const int64_t by = std::min<int64_t>(rows, 65535);
+    const int64_t bz = ft::ceil_div(rows, by);
+    return dim3((unsigned)bx, (unsigned)by, (unsigned)bz);
 }
 
 ft_status check_args(const int64_t *dims, int nd, const int64_t *kdims)
@@ -191,8 +207,9 @@ extern "C" ft_status fastconv_fft(const float *input, const int64_t *dims, int n
     }
     cudaStream_t s = ft::as_stream(stream);
     const Ext F = ext3(sh.F, nd);
-    pad_kernel<<<grid_for(sh.R), kThreads, 0, s>>>(input, ext3(dims, nd), F, sh.R, ra);
-    pad_kernel<<<grid_for(sh.R), kThreads, 0, s>>>(kernel, ext3(kdims, nd), F, sh.R, rb);
+    const dim3 pg = row_grid(F.a[0] * F.a[1], F.a[2]);
+    pad_kernel<<<pg, kThreads, 0, s>>>(input, ext3(dims, nd), F, ra);
+    pad_kernel<<<pg, kThreads, 0, s>>>(kernel, ext3(kdims, nd), F, rb);
     if ((st = ft::check_launch()) != FT_OK) return st;
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -212,7 +229,8 @@ extern "C" ft_status fastconv_fft(const float *input, const int64_t *dims, int n
             return FT_ERR_CUDA;
         }
     }
-    crop_kernel<<<grid_for(mtot), kThreads, 0, s>>>(ra, F, ext3(m, nd), mtot, out);
+    const Ext M = ext3(m, nd);
+    crop_kernel<<<row_grid(M.a[0] * M.a[1], M.a[2]), kThreads, 0, s>>>(ra, F, M, out);
     return ft::check_launch();
 }
 
