@@ -143,6 +143,21 @@ def test_fastconv_full_size_3d_sampled(kk):
     assert abs(tot - expect) <= REL * scale
 
 
+@pytest.mark.parametrize("kc", list(range(1, 18)))
+def test_fastconv_tma_and_load_paths_bitwise(kc):
+    """The copy-engine kernel and the load-path kernel (taken for an input at a 4-byte
+    offset) apply the taps of every output in the same order, so their outputs are the
+    same bits; kernels of 4 and more rows, several 128-column tiles with a ragged tail,
+    two planes."""
+    for kr in (4, 9):
+        k = scenes.normal_array((kr, kc), seed=300 + kc + kr)
+        E = scenes.uniform_array((45, 600), seed=kc + 7)
+        assert np.array_equal(_run(E, k), _run(E, k, offset=1))
+    E3 = scenes.uniform_array((2, 29, 272), seed=kc + 9)
+    k3 = scenes.normal_array((2, 5, kc), seed=kc + 11)
+    assert np.array_equal(_run(E3, k3), _run(E3, k3, offset=1))
+
+
 @pytest.mark.parametrize("kc", list(range(2, 18)))
 def test_fastconv_fma_kernel_every_width(kc):
     """The FMA-bound kernels for every kernel width they serve (2..17 columns): rows equal to the tile's rows per thread (middle phase of length one) and
