@@ -33,7 +33,7 @@ typedef enum {
     FT_OK = 0,
     FT_ERR_INVALID_ARG = 1,   /* null pointer, bad enum value, negative size */
     FT_ERR_SHAPE = 2,         /* dimensions inconsistent or too small for the request */
-    FT_ERR_UNSUPPORTED = 3,   /* valid request beyond this build's limits */
+    FT_ERR_UNSUPPORTED = 3,   /* valid request beyond the library's limits */
     FT_ERR_WORKSPACE = 4,     /* request larger than the context was created for */
     FT_ERR_CUDA = 5,          /* a CUDA runtime call failed */
     FT_ERR_TIMEOUT = 6        /* a bounded wait inside a kernel gave up (see fastconv_check) */

@@ -388,6 +388,26 @@ def test_fronto_parallel_ttc_close_to_ground_truth():
     assert abs(r1["x0"] - fx) < 3.0 and abs(r1["y0"] - fy) < 3.0
 
 
+def test_ttc_bias_converges_quadratically_in_speed():
+    """Sec. V-A estimates from two frames with the stencils centred at t + 1/2: the error
+    against the closed-form Z/W has a spatial floor (texture sampling) plus a part that
+    shrinks with the squared per-frame motion, so successive differences of the
+    relative bias between speeds W, W/2, W/4, ... fall by about 4 (a stamp at t instead
+    of t + 1/2 leaves a first-order term: the ratios fall towards 2)."""
+    for pmin, pmax in ((24, 48), (16, 32)):
+        bias = []
+        for W in (0.4, 0.2, 0.1, 0.05, 0.025):
+            sc = scenes.fronto_parallel_scene(H=96, W=96, seed=11, Z0=10.0, speed=W, pmin=pmin, pmax=pmax)
+            E0 = scenes.render(sc, 4.0).double().numpy()
+            E1 = scenes.render(sc, 5.0).double().numpy()
+            gt, _, _ = scenes.ground_truth(sc, 4.5)
+            bias.append((oracle.ttc_pair(E0, E1, levels=1, mode=0)[0]["ttc"] - gt) / gt)
+        d = np.diff(bias)
+        assert np.all(d > 0), bias
+        ratios = d[:-1] / d[1:]
+        assert np.all((ratios > 2.8) & (ratios < 4.6)), ratios
+
+
 def test_multiscale_rule_golden():
     for case in _golden("multiscale_rule.json")["cases"]:
         L = len(case["ttc"])
