@@ -218,14 +218,21 @@ conv_tma_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constan
         const T *base = cur + r0 * BW + c0 + (PADT - PADC);
         float win[PADC + 4];
         if constexpr (SMALLR) {
-            // kernels of fewer rows than OY: every (output row, kernel row) pair loads
-            // its window (Kr <= 3 loads per output row)
+            // kernels of fewer rows than OY (Kr <= 3): each of the OY + Kr - 1 staged rows
+            // is loaded once and applied to every output row it reaches (kernel row
+            // a = y + Kr - 1 - ir); rows are taken last to first, so that each output
+            // row sees its kernel rows in increasing order
 #pragma unroll
-            for (int y = 0; y < OY; ++y)
-                for (int a = 0; a < Kr; ++a) {
-                    load_window_t<T, PADC>(win, base + (y + Kr - 1 - a) * BW);
-                    fma_row<NTAP, PADC>(acc[y], win, ks4 + a * (KS / 4));
+            for (int ir = OY + 1; ir >= 0; --ir) {
+                if (ir < OY + Kr - 1) {
+                    load_window_t<T, PADC>(win, base + ir * BW);
+#pragma unroll
+                    for (int y = 0; y < OY; ++y) {
+                        const int a = y + Kr - 1 - ir;
+                        if (a >= 0 && a < Kr) fma_row<NTAP, PADC>(acc[y], win, ks4 + a * (KS / 4));
+                    }
                 }
+            }
         } else {
 #pragma unroll
         for (int ir = 0; ir < OY - 1; ++ir) {

@@ -699,8 +699,15 @@ static ft_status conv_nd_impl(const float *input, const int64_t *dims, int nd, c
         conv_direct_kernel<<<blocks, kThreads, 0, s>>>(p, tot_out);
         return ft::check_launch();
     }
-    // small kernels (at most 2 leading taps, plane kernel up to 3 x 3): streaming rows
+    // small kernels (at most 2 leading taps, plane kernel up to 3 x 3): memory-bound.
+    // Batches of 2-D planes take the copy-engine kernel (measured faster there), single
+    // planes and two leading taps the streaming rows kernel
     if (p.k_lead_total <= 2 && p.Kr <= 3 && p.Kc <= 3) {
+        if (planes >= 4 && p.k_lead_total == 1) {
+            bool used = false;
+            const ft_status st = launch_conv_tma(p, planes, s, &used);
+            if (st != FT_OK || used) return st;
+        }
         if (p.k_lead_total == 1) return launch_rows_kl<1>(p, planes, s);
         return launch_rows_kl<2>(p, planes, s);
     }
