@@ -526,6 +526,22 @@ OPS_PER_CUBE0 = 23.5
 L0_TRAFFIC_PER_PAIR = 3.86e6
 
 
+def conv_hbm_summary(rows, hbm_peak):
+    """The memory-bound FastConv rows on batches of 16 1080p FP32 images (direct path with
+    kernels of at most 5 x 5, separable path) as GB/s and fractions of the measured HBM
+    copy rate."""
+    out = []
+    for r in rows:
+        if r.get("input") != [16, 1080, 1920] or "input_dtype" in r:
+            continue
+        ks = r.get("kernel", [0, 9, 9])
+        sep = r.get("path") == "separable"
+        if sep or ("path" not in r and ks[-1] <= 5):
+            out.append({"workload": "16 x 1080 x 1920 FP32 * 1 x %d x %d%s" % (ks[1], ks[2], " (separable)" if sep else ""),
+                        "GBps": r["GBps"], "frac": r["hbm_frac"], "us": r["us"]})
+    return {"peak": hbm_peak, "unit": "GB/s", "peak_source": "measured HBM copy rate", "rows": out}
+
+
 def rank_env():
     """(world, rank, local rank) from the torch.distributed launcher's environment."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
@@ -719,6 +735,8 @@ def run_ours(args):
             "batch_uneven": batch,
             "serve": serve,
         }
+        if conv_rows:
+            line["fastconv_hbm"] = conv_hbm_summary(conv_rows, hbm_peak)
         print(json.dumps(line))
     ctx.close()
     if world > 1:
