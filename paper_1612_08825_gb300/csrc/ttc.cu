@@ -191,6 +191,34 @@ ttc_derivatives_kernel(const T0 *fa, const T0 *fb, int H, int W, int64_t pitch_e
     if (G) G[o] = fmaf((float)j + xoff, ex, ((float)i + yoff) * ey);
 }
 
+// atan2(y, x) in FP32 for the gradient direction: with t = min(|x|, |y|) / max(|x|, |y|)
+// in [0, 1], atan(t) = t P(t^2) with P the degree-8 minimax polynomial of
+// csrc/fit_atan.py (FP32 evaluation error 9.5e-8 on [0, 1]); then atan2 follows from the
+// octant: pi/2 - a when |y| > |x|, pi - a when x < 0, the sign of y.  Total error below
+// 5e-7 rad (t is correctly rounded; the two subtractions round once each).  atan2(0, 0)
+// gives +-0 (x = +0) or +-pi (x = -0), NaN inputs give NaN.
+__device__ __forceinline__ float atan2_poly(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.f ? mn / mx : 0.f;
+    const float s = t * t;
+    float p = 2.456720220e-03f;
+    p = fmaf(p, s, -1.440133899e-02f);
+    p = fmaf(p, s, 3.978119045e-02f);
+    p = fmaf(p, s, -7.234854251e-02f);
+    p = fmaf(p, s, 1.049894467e-01f);
+    p = fmaf(p, s, -1.416122913e-01f);
+    p = fmaf(p, s, 1.998590678e-01f);
+    p = fmaf(p, s, -3.333259821e-01f);
+    p = fmaf(p, s, 9.999998808e-01f);
+    float r = p * t;
+    if (ay > ax) r = 1.57079632679489662f - r;
+    if (signbit(x)) r = 3.14159265358979324f - r;
+    r = copysignf(r, y);
+    return (x != x || y != y) ? x + y : r;
+}
+
 // Gradient magnitude and direction of one image (Sec. II, Eq. Emag, Eq. Eangle): a
 // thread owns one output column and walks GR_ROWS output rows, keeping the previous
 // pixel row in registers; the right neighbour pixel comes from the next lane (the last
@@ -229,7 +257,7 @@ ttc_gradient_kernel(const T *__restrict__ img, int H, int W, int64_t pitch_e, fl
         if (inside && r < nrows) {
             const int64_t o = (int64_t)(i0 + r) * (W - 1) + j;
             if (mag) mag[o] = sqrtf(ex * ex + ey * ey);
-            if (dir) dir[o] = atan2f(ey, ex);
+            if (dir) dir[o] = atan2_poly(ey, ex);
         }
     }
 }

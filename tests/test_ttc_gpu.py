@@ -278,9 +278,12 @@ def test_full_size_video_large_tile_paths():
 
 
 def _gradient_check(E, got_mag, got_dir, integer):
-    """|E| to 1.2e-7 relative for uint8 (Ex, Ey exact), direction to 1e-6 rad (atan2f
-    is within 2 ulp); float frames add the FP32 rounding of the differences,
-    1e-6 of the block's absolute sum, propagated to the direction through 1/|E|."""
+    """|E| to 1.2e-7 relative for uint8 (Ex, Ey exact), direction to 5e-7 rad (the
+    kernel's arctangent: minimax polynomial after the octant reduction, worst case
+    4.4e-7 rad with the FP32 rounding of t, pi/2 and pi; uint8 images give millions of
+    exact (Ex, Ey) pairs, octant boundaries and axes included); float frames add the
+    FP32 rounding of the differences, 1e-6 of the block's absolute sum, propagated to
+    the direction through 1/|E|."""
     mag, ang = oracle.gradient(E)
     E = np.asarray(E, np.float64)
     blk = np.abs(E[:-1, :-1]) + np.abs(E[:-1, 1:]) + np.abs(E[1:, :-1]) + np.abs(E[1:, 1:])
@@ -289,7 +292,7 @@ def _gradient_check(E, got_mag, got_dir, integer):
     assert np.all(dm <= bound_m + 1e-30), float(np.max(dm - bound_m))
     d = np.abs(np.angle(np.exp(1j * (got_dir.astype(np.float64) - ang))))
     ok = mag > 0
-    bound_d = 1e-6 + (np.zeros_like(mag) if integer else 1e-6 * blk / np.maximum(mag, 1e-300))
+    bound_d = 5e-7 + (np.zeros_like(mag) if integer else 1e-6 * blk / np.maximum(mag, 1e-300))
     assert np.all(d[ok] <= bound_d[ok]), float(np.max(d[ok] - bound_d[ok]))
     assert np.all(np.abs(got_dir) <= np.float32(np.pi))
 
