@@ -317,7 +317,8 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
 
 def gradient_bench(dev, hbm_peak, reps):
     """Gradient magnitude and direction (Sec. II) of one 1080p uint8 image and of 16
-    images: bytes = pixels read once + two float outputs written."""
+    images (one launch per image, and one batched launch): bytes = pixels read once +
+    two float outputs written."""
     import torch
     import paper_1612_08825_gb300 as ft
     import scenes
@@ -326,25 +327,32 @@ def gradient_bench(dev, hbm_peak, reps):
     sc = scenes.tilted_plane_scene(H=H, W=W, seed=5)
     img = scenes.render(sc, 0.0, device=dev)
     s = torch.cuda.current_stream(dev)
-    for n in (1, 16):
-        imgs = [img.clone() for _ in range(n)]
-        outs = [(torch.empty((H - 1, W - 1), device=dev), torch.empty((H - 1, W - 1), device=dev)) for _ in range(n)]
-        L = ft.load()
+    L = ft.load()
+    for n, batched in ((1, False), (16, False), (16, True)):
+        stack = img.unsqueeze(0).repeat(n, 1, 1).contiguous()
+        mags = torch.empty((n, H - 1, W - 1), device=dev)
+        angs = torch.empty((n, H - 1, W - 1), device=dev)
         ts = []
         for i in range(reps + 2):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(s)
-            for im, (m, a) in zip(imgs, outs):
-                L.ttc_gradient(im.data_ptr(), 0, H, W, W, m.data_ptr(), a.data_ptr(), s.cuda_stream)
+            if batched:      # one launch for the batch
+                L.ttc_gradient_batch(stack.data_ptr(), n, H * W, 0, H, W, W, mags.data_ptr(), angs.data_ptr(),
+                                     s.cuda_stream)
+            else:            # one launch per image
+                for k in range(n):
+                    L.ttc_gradient(stack[k].data_ptr(), 0, H, W, W, mags[k].data_ptr(), angs[k].data_ptr(),
+                                   s.cuda_stream)
             e1.record(s)
             ts.append((e0, e1))
         torch.cuda.synchronize(dev)
         t = float(np.median([a.elapsed_time(b) for a, b in ts[2:]])) * 1e-3
         byts = n * (H * W + 8 * (H - 1) * (W - 1))
-        rows.append({"images": n, "H": H, "W": W, "dtype": "u8", "us": t * 1e6, "GBps": byts / t / 1e9,
-                     "hbm_frac": byts / t / 1e9 / hbm_peak, "algorithmic_bytes": byts})
+        rows.append({"images": n, "launches": 1 if batched or n == 1 else n, "H": H, "W": W, "dtype": "u8",
+                     "us": t * 1e6, "GBps": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / hbm_peak,
+                     "algorithmic_bytes": byts})
     del flush
     return rows
 

@@ -294,6 +294,19 @@ ft_status ttc_gradient(const void *image, int dtype, int H, int W, int64_t pitch
                        void *stream);
 
 /*
+ * ttc_gradient for n images of one size in one launch (a batch of frames):
+ *   images : device, image i at images + i * image_stride_bytes (each H rows of W pixels,
+ *            row stride pitch_bytes);
+ *   mag, dir : device, n x (H-1) x (W-1) floats each (image i's outputs at
+ *              i * (H-1) * (W-1)), either may be NULL (not both).
+ * Errors: those of ttc_gradient, and FT_ERR_SHAPE for n < 1 or an image stride smaller
+ * than H rows (image_stride_bytes < (H-1) * pitch_bytes + W * pixel size, for n > 1),
+ * FT_ERR_UNSUPPORTED for n > 65535.
+ */
+ft_status ttc_gradient_batch(const void *images, int n, int64_t image_stride_bytes, int dtype, int H, int W,
+                             int64_t pitch_bytes, float *mag, float *dir, void *stream);
+
+/*
  * The same for the T-1 consecutive pairs (t, t+1) of a video of T frames stored
  * frame_stride_bytes apart: out[(t * levels) + l] for pair t, level l (device,
  * (T-1) * levels results).  Sec. V-B: the estimate is produced at every frame.

@@ -117,6 +117,9 @@ def load(path: Optional[str] = None):
     L.ttc_derivatives.restype = st
     L.ttc_gradient.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp]
     L.ttc_gradient.restype = st
+    L.ttc_gradient_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int64, _vp, _vp, _vp]
+    L.ttc_gradient_batch.restype = st
     L.ttc_ctx_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.ttc_ctx_create.restype = st
     L.ttc_ctx_destroy.argtypes = [_vp]
@@ -381,21 +384,28 @@ def ttc_derivatives(prev: torch.Tensor, cur: torch.Tensor, with_G: bool = True):
 
 
 def gradient(image: torch.Tensor, with_mag: bool = True, with_dir: bool = True):
-    """Gradient magnitude and direction of one image (Sec. II, Eq. Emag, Eq. Eangle):
-    two (H-1) x (W-1) float32 tensors (None for an output not asked for)."""
+    """Gradient magnitude and direction (Sec. II, Eq. Emag, Eq. Eangle) of one image (2-D)
+    or of a batch of images (3-D, one launch): float32 tensors of shape (..., H-1, W-1)
+    (None for an output not asked for)."""
     L = load()
     _require_cuda(image, "image")
-    if image.dim() != 2 or image.stride(1) != 1:
-        raise ValueError("image must be 2-D with contiguous rows")
+    if image.dim() not in (2, 3) or image.stride(-1) != 1:
+        raise ValueError("image must be 2-D (or a 3-D batch) with contiguous rows")
     if not (with_mag or with_dir):
         raise ValueError("ask for at least one output")
     dt, es = _frame_args(image)
-    H, W = image.shape
-    mag = torch.empty((H - 1, W - 1), dtype=torch.float32, device=image.device) if with_mag else None
-    ang = torch.empty((H - 1, W - 1), dtype=torch.float32, device=image.device) if with_dir else None
-    _check(L.ttc_gradient(image.data_ptr(), dt, H, W, image.stride(0) * es,
-                          mag.data_ptr() if mag is not None else None, ang.data_ptr() if ang is not None else None,
-                          _stream_ptr(image)), "ttc_gradient")
+    H, W = image.shape[-2:]
+    n = image.shape[0] if image.dim() == 3 else 1
+    shape = (n, H - 1, W - 1) if image.dim() == 3 else (H - 1, W - 1)
+    mag = torch.empty(shape, dtype=torch.float32, device=image.device) if with_mag else None
+    ang = torch.empty(shape, dtype=torch.float32, device=image.device) if with_dir else None
+    if n == 0:
+        return mag, ang
+    stride = image.stride(0) * es if image.dim() == 3 else 0
+    _check(L.ttc_gradient_batch(image.data_ptr(), n, stride, dt, H, W, image.stride(-2) * es,
+                                mag.data_ptr() if mag is not None else None,
+                                ang.data_ptr() if ang is not None else None, _stream_ptr(image)),
+           "ttc_gradient_batch")
     return mag, ang
 
 

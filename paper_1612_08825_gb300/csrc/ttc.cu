@@ -227,9 +227,14 @@ constexpr int GR_ROWS = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-ttc_gradient_kernel(const T *__restrict__ img, int H, int W, int64_t pitch_e, float *__restrict__ mag,
-                    float *__restrict__ dir)
+ttc_gradient_kernel(const T *__restrict__ img, int H, int W, int64_t pitch_e, int64_t image_stride_e,
+                    float *__restrict__ mag, float *__restrict__ dir)
 {
+    // image blockIdx.z of the batch
+    img += (int64_t)blockIdx.z * image_stride_e;
+    const int64_t out_off = (int64_t)blockIdx.z * (H - 1) * (W - 1);
+    if (mag) mag += out_off;
+    if (dir) dir += out_off;
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * 256 + threadIdx.x;      // output column
     const int i0 = blockIdx.y * GR_ROWS;               // first output row
@@ -1240,22 +1245,33 @@ extern "C" ft_status ttc_derivatives(const void *prev, const void *cur, int dtyp
     return ft::check_launch();
 }
 
-extern "C" ft_status ttc_gradient(const void *image, int dtype, int H, int W, int64_t pitch_bytes, float *mag,
-                                  float *dir, void *stream)
+extern "C" ft_status ttc_gradient_batch(const void *images, int n, int64_t image_stride_bytes, int dtype, int H,
+                                        int W, int64_t pitch_bytes, float *mag, float *dir, void *stream)
 {
-    if (!image || (!mag && !dir)) return FT_ERR_INVALID_ARG;
+    if (!images || (!mag && !dir)) return FT_ERR_INVALID_ARG;
     const ft_status st = check_frames(dtype, H, W, pitch_bytes);
     if (st != FT_OK) return st;
-    const dim3 grid((unsigned)ft::ceil_div(W - 1, 256), (unsigned)ft::ceil_div(H - 1, GR_ROWS));
+    const int es = elem_size(dtype);
+    if (n < 1) return FT_ERR_SHAPE;
+    if (n > 1 && image_stride_bytes < (int64_t)(H - 1) * pitch_bytes + (int64_t)W * es) return FT_ERR_SHAPE;
+    if (n > 65535) return FT_ERR_UNSUPPORTED;
+    if (image_stride_bytes % es) return FT_ERR_SHAPE;
+    const dim3 grid((unsigned)ft::ceil_div(W - 1, 256), (unsigned)ft::ceil_div(H - 1, GR_ROWS), (unsigned)n);
     if (grid.y > 65535) return FT_ERR_UNSUPPORTED;
     cudaStream_t s = ft::as_stream(stream);
     if (dtype == FT_U8)
-        ttc_gradient_kernel<unsigned char><<<grid, 256, 0, s>>>(static_cast<const unsigned char *>(image), H, W,
-                                                                pitch_bytes, mag, dir);
+        ttc_gradient_kernel<unsigned char><<<grid, 256, 0, s>>>(static_cast<const unsigned char *>(images), H, W,
+                                                                pitch_bytes, image_stride_bytes, mag, dir);
     else
-        ttc_gradient_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(image), H, W, pitch_bytes / 4,
-                                                        mag, dir);
+        ttc_gradient_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(images), H, W, pitch_bytes / 4,
+                                                        image_stride_bytes / 4, mag, dir);
     return ft::check_launch();
+}
+
+extern "C" ft_status ttc_gradient(const void *image, int dtype, int H, int W, int64_t pitch_bytes, float *mag,
+                                  float *dir, void *stream)
+{
+    return ttc_gradient_batch(image, 1, 0, dtype, H, W, pitch_bytes, mag, dir, stream);
 }
 
 extern "C" int ttc_select_level(const ttc_level_result *r, int levels, int rule)

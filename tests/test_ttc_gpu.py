@@ -320,6 +320,39 @@ def test_gradient_odd_shapes_pitch_and_dtypes(H, W, pad, offset):
     assert none is None and torch.equal(m_only, mag)
 
 
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_gradient_batch_equals_single_images(dtype):
+    """One launch over a batch (3-D input, image stride larger than the image) gives
+    each image's outputs bitwise as the single-image call, and matches the oracle."""
+    rng = np.random.default_rng(7)
+    H, W, n = 37, 53, 5
+    if dtype == "u8":
+        big = torch.from_numpy(rng.integers(0, 256, (n, H + 3, W + 5), dtype=np.uint8)).to(DEV)
+    else:
+        big = torch.from_numpy(rng.random((n, H + 3, W + 5), dtype=np.float32)).to(DEV)
+    batch = big[:, :H, :W]                      # row pitch W + 5, image stride (H + 3)(W + 5)
+    mag, ang = ft.gradient(batch)
+    assert mag.shape == (n, H - 1, W - 1)
+    for k in range(n):
+        m1, a1 = ft.gradient(batch[k])
+        assert torch.equal(m1, mag[k]) and torch.equal(a1, ang[k])
+        _gradient_check(batch[k].cpu().numpy(), mag[k].cpu().numpy(), ang[k].cpu().numpy(), dtype == "u8")
+
+
+def test_gradient_batch_errors():
+    L = ft.load()
+    x = torch.zeros((3, 4, 4), dtype=torch.uint8, device=DEV)
+    out = torch.empty((3, 3, 3), device=DEV)
+    assert L.ttc_gradient_batch(x.data_ptr(), 0, 16, 0, 4, 4, 4, out.data_ptr(), None, None) == 2
+    assert L.ttc_gradient_batch(x.data_ptr(), 3, 8, 0, 4, 4, 4, out.data_ptr(), None, None) == 2
+    assert L.ttc_gradient_batch(x.data_ptr(), 70000, 16, 0, 4, 4, 4, out.data_ptr(), None, None) == 3
+    assert L.ttc_gradient_batch(None, 3, 16, 0, 4, 4, 4, out.data_ptr(), None, None) == 1
+    assert L.ttc_gradient_batch(x.data_ptr(), 3, 16, 0, 4, 4, 4, out.data_ptr(), None, None) == 0
+    torch.cuda.synchronize()
+    m, _ = ft.gradient(torch.zeros((0, 4, 4), dtype=torch.uint8, device=DEV), with_dir=False)
+    assert m.shape == (0, 3, 3)
+
+
 def test_gradient_errors():
     L = ft.load()
     x = torch.zeros((4, 4), dtype=torch.uint8, device=DEV)
