@@ -219,10 +219,11 @@ __device__ __forceinline__ float atan2_poly(float y, float x)
     return (x != x || y != y) ? x + y : r;
 }
 
-// Gradient magnitude and direction of one image (Sec. II, Eq. Emag, Eq. Eangle): a
-// thread owns one output column and walks GR_ROWS output rows, keeping the previous
-// pixel row in registers; the right neighbour pixel comes from the next lane (the last
-// lane of a warp loads its own).  Stores are coalesced rows; HBM-bound.
+// Gradient magnitude and direction (Sec. II, Eq. Emag, Eq. Eangle) of image blockIdx.z
+// of a batch: a thread owns one output column and walks GR_ROWS output rows, keeping
+// the previous pixel row in registers; the right neighbour pixel comes from the next
+// lane (the last lane of a warp loads its own).  Stores are coalesced rows.  One image
+// of 1080p is a single short wave (latency-bound); batches fill the GPU.
 constexpr int GR_ROWS = 8;
 
 template <typename T>
