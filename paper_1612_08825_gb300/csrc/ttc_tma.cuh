@@ -154,7 +154,7 @@ ttc_pass_tma_kernel(const __grid_constant__ CUtensorMap ma, const __grid_constan
     for (int t = t0; t < tp.total; t += gridDim.x, ++k) {
         const int b = k & 1;
         const int tn = t + gridDim.x;
-        // the other buffer was released by the barrier that ended the previous tile
+        // the other buffer was released by the barrier inside the previous tile's reduction
         if (tid == 0 && tn < tp.total) issue_tile(tp, &ma, &mb, &xa, &xb, tn, bufs + (b ^ 1) * BUF, &bar[b ^ 1]);
         const bool ok = mbar_wait(&bar[b], (k >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -178,8 +178,13 @@ ttc_pass_tma_kernel(const __grid_constant__ CUtensorMap ma, const __grid_constan
         float acc[NSUM];
 #pragma unroll
         for (int s = 0; s < NSUM; ++s) acc[s] = acc2[s].x + acc2[s].y;
+        // no CTA barrier after the reduction: its own barrier (between the scratch writes
+        // and reads) already follows every thread's reads of buffer b, which the next
+        // tile's copy refills, and the next tile's barrier after its wait follows every
+        // read of the scratch, which the next reduction rewrites.  The warp barrier keeps
+        // the compiler from moving the next tile's code into this one (registers).
         block_reduce(acc, red, p.partials + ((int64_t)pair * p.ntiles + tile) * NSUM);
-        __syncthreads();      // buffer b and the reduction scratch are free again
+        __syncwarp();
     }
 }
 
