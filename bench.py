@@ -159,7 +159,8 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(_config(T_FRAMES), sample=f"{pairs_per_step} pairs of the video per step"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{pairs_per_step} 1080p pairs x {args.steps} steps, 5 levels, FOE"},
+                         "sample": f"{pairs_per_step} 1080p pairs x {args.steps} steps, 5 levels, FOE",
+                         "nproc": host_cpu()["nproc"], "cpu_model": host_cpu()["model"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -550,6 +551,29 @@ def conv_hbm_summary(rows, hbm_peak):
     return {"peak": hbm_peak, "unit": "GB/s", "peak_source": "measured HBM copy rate", "rows": out}
 
 
+def host_cpu():
+    """Host core count and CPU model name (for the CPU baseline's record)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "Model name", "cpu model"):
+            for line in txt.splitlines():
+                if line.split(":")[0].strip() == key:
+                    model = line.split(":", 1)[1].strip()
+                    break
+            if model:
+                break
+        if not model:
+            impl = [l.split(":", 1)[1].strip() for l in txt.splitlines() if l.startswith("CPU implementer")]
+            part = [l.split(":", 1)[1].strip() for l in txt.splitlines() if l.startswith("CPU part")]
+            if impl and part:
+                model = f"Arm CPU implementer {impl[0]} part {part[0]}"
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count() or 1, "model": model or "unknown"}
+
+
 def rank_env():
     """(world, rank, local rank) from the torch.distributed launcher's environment."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
@@ -661,8 +685,16 @@ def run_ours(args):
             if time.perf_counter() - t0 > args.cpu_seconds:
                 break
         dt_cpu = time.perf_counter() - t0
+        info = host_cpu()
         cpu = {"value": n_done / dt_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n_done} pairs of the same video, 5 levels, FOE, single thread"}
+               "sample": f"first {n_done} pairs of the same video, 5 levels, FOE, single thread",
+               "us_per_pair": dt_cpu / max(n_done, 1) * 1e6, "nproc": info["nproc"], "cpu_model": info["model"]}
+        # the same oracle, one pair per process at a time, over all host cores
+        nw = info["nproc"]
+        npar = min(host.shape[0] - 1, 2 * nw)
+        _, dt_par = oracle.ttc_pairs_parallel(host, npar, LEVELS, 1, nw)
+        cpu["all_cores"] = {"value": npar / dt_par, "unit": UNIT, "cores": nw, "kind": "oracle",
+                            "sample": f"first {npar} pairs of the same video over {nw} spawned processes"}
         parity = {"pairs_checked": n_done, "max_sum_err_rel_abssum": worst, "tolerance": 1e-5}
 
     # e2e through the public API with pinned host frames: H2D of the video (in chunks

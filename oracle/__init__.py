@@ -190,3 +190,26 @@ def select_level(results: np.ndarray, rule: int = 0) -> int:
     """Multi-scale selection (Sec. V-B) over per-level results of one pair."""
     r = np.ascontiguousarray(results, dtype=RESULT_DTYPE)
     return int(_load().oracle_select_level(r.ctypes.data, r.shape[0], int(rule)))
+
+
+def _pair_job(job):
+    prev, cur, levels, mode = job
+    return ttc_pair(prev, cur, levels=levels, mode=mode)
+
+
+def ttc_pairs_parallel(frames, npairs: int, levels: int, mode: int, workers: int):
+    """ttc_pair on the first npairs consecutive pairs of `frames` (host array) spread over
+    `workers` processes (spawned, so that a process that already uses the GPU can call
+    it); returns (results, seconds of the timed pass).  A first untimed pass starts the
+    processes and loads the library in each; for timing the baseline on all host cores."""
+    import multiprocessing as mp
+    import time
+
+    build()
+    jobs = [(frames[t], frames[t + 1], levels, mode) for t in range(npairs)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        pool.map(_pair_job, jobs[:workers], chunksize=1)
+        t0 = time.perf_counter()
+        out = pool.map(_pair_job, jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+    return out, dt
