@@ -358,6 +358,50 @@ def gradient_bench(dev, hbm_peak, reps):
     return rows
 
 
+def small_bench(dev, reps=50):
+    """The plain single-scale case: 32 float32 frames of 128 x 128 (a fronto-parallel plane
+    approaching at W = 0.1 per frame from Z0 = 10), all 31 pairs in one call, TTC-only
+    (C = -sum(G Et) / sum(G^2)) and FOE; and one 128 x 128 (*) 3 x 3 N(0,1) full
+    convolution.  Too small for a roofline: latency per call as a caller sees it (CUDA
+    events around the Python call, so the host-side marshalling gap before the launch,
+    during which the GPU waits, is included) and per pair."""
+    import torch
+    import paper_1612_08825_gb300 as ft
+    import scenes
+    sc = scenes.fronto_parallel_scene(H=128, W=128, seed=0, Z0=10.0, speed=0.1)
+    fr = scenes.render_sequence(sc, 32, device=dev)
+    ctx = ft.TtcContext(128, 128, 1, 31, device=dev)
+    out = ctx.new_results(31)
+    s = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            ts.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        return float(np.median([a.elapsed_time(b) for a, b in ts])) * 1e3
+
+    row = {"workload": "32 float32 frames 128 x 128, 31 pairs per call, 1 level",
+           "timing": "CUDA events around the Python call (includes the launch gap)"}
+    for name, mode in (("ttc_only", ft.MODE_TTC), ("foe", ft.MODE_FOE)):
+        us = timed(lambda: ctx.solve_sequence(fr, levels=1, mode=mode, out=out))
+        row[name] = {"us_per_call": us, "us_per_pair": us / 31}
+    ctx.close()
+    x = torch.from_numpy(scenes.uniform_array((128, 128), seed=1)).to(dev)
+    k = torch.from_numpy(scenes.normal_array((3, 3), seed=2)).to(dev)
+    y = ft.fastconv_nd(x, k)
+    row["conv_128x128_3x3_us"] = timed(lambda: ft.fastconv_nd(x, k, out=y))
+    return row
+
+
 def batch_bench(dev, args):
     """512 independent pairs of uneven sizes: autotuned work-list launches replayed from
     a CUDA graph, against the plain per-frame path (one ttc_solve per pair)."""
@@ -729,6 +773,8 @@ def run_ours(args):
     if rank == 0 and not args.no_batch:
         batch = batch_bench(dev, args)
 
+    small = small_bench(dev) if rank == 0 else None
+
     serve = None
     if rank == 0 and not args.no_serve:
         serve = serve_bench(dev, args)
@@ -774,6 +820,7 @@ def run_ours(args):
             "gradient": grad_rows,
             "batch_uneven": batch,
             "serve": serve,
+            "plain_ttc_128": small,
         }
         if conv_rows:
             line["fastconv_hbm"] = conv_hbm_summary(conv_rows, hbm_peak)
