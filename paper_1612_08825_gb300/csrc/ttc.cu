@@ -195,13 +195,23 @@ ttc_derivatives_kernel(const T0 *fa, const T0 *fb, int H, int W, int64_t pitch_e
 // in [0, 1], atan(t) = t P(t^2) with P the degree-8 minimax polynomial of
 // csrc/fit_atan.py (FP32 evaluation error 9.5e-8 on [0, 1]); then atan2 follows from the
 // octant: pi/2 - a when |y| > |x|, pi - a when x < 0, the sign of y.  Total error below
-// 5e-7 rad (t is correctly rounded; the two subtractions round once each).  atan2(0, 0)
+// 5e-7 rad (t within about half an ulp; the two subtractions round once each).  atan2(0, 0)
 // gives +-0 (x = +0) or +-pi (x = -0), NaN inputs give NaN.
 __device__ __forceinline__ float atan2_poly(float y, float x)
 {
     const float ax = fabsf(x), ay = fabsf(y);
     const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    const float t = mx > 0.f ? mn / mx : 0.f;
+    // t = mn / mx: approximate reciprocal, then one correction of the quotient with its
+    // exact residual (fma), which leaves t within about half an ulp; mx of at least 2^-100
+    // (any gradient of real images) keeps the reciprocal finite, smaller mx divides exactly
+    float t = 0.f;
+    if (mx >= 7.8886091e-31f) {
+        const float rc = __fdividef(1.f, mx);
+        const float q = mn * rc;
+        t = fmaf(fmaf(-q, mx, mn), rc, q);
+    } else if (mx > 0.f) {
+        t = mn / mx;
+    }
     const float s = t * t;
     float p = 2.456720220e-03f;
     p = fmaf(p, s, -1.440133899e-02f);
@@ -226,16 +236,11 @@ __device__ __forceinline__ float atan2_poly(float y, float x)
 // of 1080p is a single short wave (latency-bound); batches fill the GPU.
 constexpr int GR_ROWS = 8;
 
-template <typename T>
+template <typename T, bool MAG, bool DIR>
 __global__ void __launch_bounds__(256)
 ttc_gradient_kernel(const T *__restrict__ img, int H, int W, int64_t pitch_e, int64_t image_stride_e,
                     float *__restrict__ mag, float *__restrict__ dir)
 {
-    // image blockIdx.z of the batch
-    img += (int64_t)blockIdx.z * image_stride_e;
-    const int64_t out_off = (int64_t)blockIdx.z * (H - 1) * (W - 1);
-    if (mag) mag += out_off;
-    if (dir) dir += out_off;
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * 256 + threadIdx.x;      // output column
     const int i0 = blockIdx.y * GR_ROWS;               // first output row
@@ -243,29 +248,49 @@ ttc_gradient_kernel(const T *__restrict__ img, int H, int W, int64_t pitch_e, in
     const int jc = inside ? j : W - 2;                 // clamped column for loads
     const int nrows = min(GR_ROWS, H - 1 - i0);        // output rows of this block (>= 1)
     const bool own = lane == 31 || jc + 1 >= W - 1;    // the right neighbour is not in the next lane
+    // image blockIdx.z of the batch; this thread's first output of each kind
+    img += (int64_t)blockIdx.z * image_stride_e;
+    const int64_t o0 = ((int64_t)blockIdx.z * (H - 1) + i0) * (W - 1) + j;
     // all pixel loads first (rows i0 .. i0 + nrows; rows past the image repeat the last)
     float c0[GR_ROWS + 1], c1[GR_ROWS + 1];
+    const T *row = img + (int64_t)i0 * pitch_e + jc;
 #pragma unroll
     for (int r = 0; r <= GR_ROWS; ++r) {
-        const T *row = img + (int64_t)(i0 + min(r, nrows)) * pitch_e;
-        c0[r] = (float)__ldg(row + jc);
-        c1[r] = own ? (float)__ldg(row + jc + 1) : 0.f;
+        c0[r] = (float)__ldg(row);
+        c1[r] = own ? (float)__ldg(row + 1) : 0.f;
+        if (r < nrows) row += pitch_e;
     }
 #pragma unroll
     for (int r = 0; r <= GR_ROWS; ++r) {
         const float n = __shfl_down_sync(0xffffffffu, c0[r], 1);
         if (!own) c1[r] = n;
     }
+    if (!inside) return;
+    float *pm = MAG ? mag + o0 : nullptr;
+    float *pd = DIR ? dir + o0 : nullptr;
 #pragma unroll
     for (int r = 0; r < GR_ROWS; ++r) {
+        if (r >= nrows) break;
         const float ex = 0.5f * ((c1[r] - c0[r]) + (c1[r + 1] - c0[r + 1]));
         const float ey = 0.5f * ((c0[r + 1] - c0[r]) + (c1[r + 1] - c1[r]));
-        if (inside && r < nrows) {
-            const int64_t o = (int64_t)(i0 + r) * (W - 1) + j;
-            if (mag) mag[o] = sqrtf(ex * ex + ey * ey);
-            if (dir) dir[o] = atan2_poly(ey, ex);
+        if (MAG) {
+            *pm = sqrtf(ex * ex + ey * ey);
+            pm += W - 1;
+        }
+        if (DIR) {
+            *pd = atan2_poly(ey, ex);
+            pd += W - 1;
         }
     }
+}
+
+template <typename T>
+void launch_gradient(const T *img, int H, int W, int64_t pitch_e, int64_t stride_e, float *mag, float *dir,
+                     dim3 grid, cudaStream_t s)
+{
+    if (mag && dir) ttc_gradient_kernel<T, true, true><<<grid, 256, 0, s>>>(img, H, W, pitch_e, stride_e, mag, dir);
+    else if (mag) ttc_gradient_kernel<T, true, false><<<grid, 256, 0, s>>>(img, H, W, pitch_e, stride_e, mag, dir);
+    else ttc_gradient_kernel<T, false, true><<<grid, 256, 0, s>>>(img, H, W, pitch_e, stride_e, mag, dir);
 }
 
 // ---------------------------------------------------------------------------
@@ -1261,11 +1286,11 @@ extern "C" ft_status ttc_gradient_batch(const void *images, int n, int64_t image
     if (grid.y > 65535) return FT_ERR_UNSUPPORTED;
     cudaStream_t s = ft::as_stream(stream);
     if (dtype == FT_U8)
-        ttc_gradient_kernel<unsigned char><<<grid, 256, 0, s>>>(static_cast<const unsigned char *>(images), H, W,
-                                                                pitch_bytes, image_stride_bytes, mag, dir);
+        launch_gradient(static_cast<const unsigned char *>(images), H, W, pitch_bytes, image_stride_bytes, mag, dir,
+                        grid, s);
     else
-        ttc_gradient_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(images), H, W, pitch_bytes / 4,
-                                                        image_stride_bytes / 4, mag, dir);
+        launch_gradient(static_cast<const float *>(images), H, W, pitch_bytes / 4, image_stride_bytes / 4, mag, dir,
+                        grid, s);
     return ft::check_launch();
 }
 
