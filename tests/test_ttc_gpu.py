@@ -347,6 +347,9 @@ def test_gradient_batch_errors():
     assert L.ttc_gradient_batch(x.data_ptr(), 3, 8, 0, 4, 4, 4, out.data_ptr(), None, None) == 2
     assert L.ttc_gradient_batch(x.data_ptr(), 70000, 16, 0, 4, 4, 4, out.data_ptr(), None, None) == 3
     assert L.ttc_gradient_batch(None, 3, 16, 0, 4, 4, 4, out.data_ptr(), None, None) == 1
+    xf = torch.zeros((2, 4, 4), dtype=torch.float32, device=DEV)
+    # float images 66 bytes apart: not a whole number of pixels
+    assert L.ttc_gradient_batch(xf.data_ptr(), 2, 66, 1, 4, 4, 16, out.data_ptr(), None, None) == 2
     assert L.ttc_gradient_batch(x.data_ptr(), 3, 16, 0, 4, 4, 4, out.data_ptr(), None, None) == 0
     torch.cuda.synchronize()
     m, _ = ft.gradient(torch.zeros((0, 4, 4), dtype=torch.uint8, device=DEV), with_dir=False)
