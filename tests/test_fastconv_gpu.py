@@ -45,6 +45,7 @@ def _check_full(E, k, offset=0):
     ((99, 257), (7, 7)), ((66, 140), (15, 15)), ((40, 37), (1, 6)), ((33, 50), (9, 1)),
     ((3, 4), (6, 9)),                        # kernel larger than the input
     ((5, 37, 45), (2, 3, 4)), ((9, 40, 33), (5, 5, 5)), ((4, 3, 20, 21), (2, 1, 3, 2)),
+    ((6, 1, 300), (1, 1, 3)), ((5, 2, 132), (1, 2, 2)), ((4, 70, 264), (1, 3, 3)),   # batches, small kernels
     ((2, 2, 2, 2, 2, 2, 3, 5), (2, 1, 2, 1, 2, 1, 2, 3)),   # rank 8
 ])
 def test_fastconv_small_shapes(shape, kshape):
