@@ -119,7 +119,7 @@ ft_status fastconv_fft(const float *input, const int64_t *dims, int nd, const fl
  * this request (kernels of at least FT_FFT_MIN_TAPS taps, rank <= 3), 0 otherwise.
  * FT_FFT_MIN_TAPS is the crossover measured on GB300 for 1080 x 1920 images.
  */
-#define FT_FFT_MIN_TAPS 1089   /* 33 x 33: direct 116 us at 31 x 31, FFT 125 us, direct 215 us at 41 x 41 */
+#define FT_FFT_MIN_TAPS 961    /* 31 x 31: direct 86 us at 25 x 25 and 117 us at 31 x 31, FFT 109 us */
 int fastconv_prefers_fft(const int64_t *dims, int nd, const int64_t *kdims);
 
 /*

@@ -90,19 +90,25 @@ struct Ext {
 };
 
 // dst (F extents, all R values) = src (N extents) zero-padded at the high end: block
-// row blockIdx.y of the grid is destination row r = z * F1 + y, threads stride its
-// columns (no divisions per element)
+// row blockIdx.y of the grid is destination row r = z * F1 + y; a block covers RSEG
+// columns of it, four consecutive ones per thread (no divisions per element)
+constexpr int RSEG = 4 * kThreads;
+
 __global__ void __launch_bounds__(kThreads) pad_kernel(const float *__restrict__ src, Ext N, Ext F,
                                                        float *__restrict__ dst)
 {
     const int64_t r = blockIdx.y + (int64_t)blockIdx.z * gridDim.y;
     if (r >= F.a[0] * F.a[1]) return;
     const int64_t z = r / F.a[1], y = r - z * F.a[1];
-    const bool row_in = z < N.a[0] && y < N.a[1];
+    const int64_t nx = (z < N.a[0] && y < N.a[1]) ? N.a[2] : 0;     // source columns of this row
     const float *s = src + (z * N.a[1] + y) * N.a[2];
     float *d = dst + r * F.a[2];
-    for (int64_t x = blockIdx.x * (int64_t)kThreads + threadIdx.x; x < F.a[2]; x += (int64_t)gridDim.x * kThreads)
-        d[x] = (row_in && x < N.a[2]) ? __ldg(s + x) : 0.f;
+    const int64_t x0 = (int64_t)blockIdx.x * RSEG + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t x = x0 + k * kThreads;
+        if (x < F.a[2]) d[x] = x < nx ? __ldg(s + x) : 0.f;
+    }
 }
 
 // a[i] = a[i] * b[i] * scale
@@ -115,7 +121,8 @@ __global__ void __launch_bounds__(kThreads) mul_kernel(cufftComplex *__restrict_
     }
 }
 
-// out (M extents) = the M corner of src (F extents), one block row per output row
+// out (M extents) = the M corner of src (F extents), one block row per output row, RSEG
+// columns per block
 __global__ void __launch_bounds__(kThreads) crop_kernel(const float *__restrict__ src, Ext F, Ext M,
                                                         float *__restrict__ out)
 {
@@ -124,8 +131,12 @@ __global__ void __launch_bounds__(kThreads) crop_kernel(const float *__restrict_
     const int64_t z = r / M.a[1], y = r - z * M.a[1];
     const float *s = src + (z * F.a[1] + y) * F.a[2];
     float *o = out + r * M.a[2];
-    for (int64_t x = blockIdx.x * (int64_t)kThreads + threadIdx.x; x < M.a[2]; x += (int64_t)gridDim.x * kThreads)
-        o[x] = s[x];
+    const int64_t x0 = (int64_t)blockIdx.x * RSEG + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t x = x0 + k * kThreads;
+        if (x < M.a[2]) o[x] = __ldg(s + x);
+    }
 }
 
 Ext ext3(const int64_t *v, int nd)
@@ -141,10 +152,10 @@ unsigned grid_for(int64_t n)
     return (unsigned)(b < 152 * 16 ? b : 152 * 16);
 }
 
-// grid for a row kernel: x over the columns (at most 8 blocks), y * z over the rows
+// grid for a row kernel: x over the columns (RSEG per block), y * z over the rows
 dim3 row_grid(int64_t rows, int64_t cols)
 {
-    const int64_t bx = std::min<int64_t>(ft::ceil_div(cols, kThreads), 8);
+    const int64_t bx = ft::ceil_div(cols, RSEG);
     const int64_t by = std::min<int64_t>(rows, 65535);
     const int64_t bz = ft::ceil_div(rows, by);
     return dim3((unsigned)bx, (unsigned)by, (unsigned)bz);

@@ -320,8 +320,8 @@ def test_fastconv_fft_errors_and_auto_switch():
     small = ft.fastconv(x, k)                                   # below the threshold: direct
     big = ft.fastconv(x, torch.rand((41, 41), device=dev))      # at or above: FFT
     assert small.shape == (68, 68) and big.shape == (104, 104)
-    assert L.fastconv_prefers_fft((ctypes.c_int64 * 2)(64, 64), 2, (ctypes.c_int64 * 2)(31, 31)) == 0
-    assert L.fastconv_prefers_fft((ctypes.c_int64 * 2)(64, 64), 2, (ctypes.c_int64 * 2)(33, 33)) == 1
+    assert L.fastconv_prefers_fft((ctypes.c_int64 * 2)(64, 64), 2, (ctypes.c_int64 * 2)(29, 29)) == 0
+    assert L.fastconv_prefers_fft((ctypes.c_int64 * 2)(64, 64), 2, (ctypes.c_int64 * 2)(31, 31)) == 1
 
 
 def _fft_small_workspace(L, x, k):
