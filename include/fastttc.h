@@ -269,7 +269,8 @@ ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, int dtype, 
  * single pair up to 1920 x 1080 with up to FT_MAX_LEVELS levels in either dtype;
  * larger requests are rejected with FT_ERR_WORKSPACE before anything is launched.
  * The first call on a device looks up the array's device address for that device
- * (with that device current); make that first call before any stream capture.
+ * (with that device current), and a call looks it up again when the device's current
+ * context has changed since; make the first call before any stream capture.
  * Every call uses the same array and leaves the last call's contents in it: nothing
  * there needs to start at zero (each call writes every value it reads), but calls
  * whose work overlaps on the GPU (other streams, other host threads) race on it, so

@@ -213,3 +213,27 @@ def ttc_pairs_parallel(frames, npairs: int, levels: int, mode: int, workers: int
         out = pool.map(_pair_job, jobs, chunksize=1)
         dt = time.perf_counter() - t0
     return out, dt
+
+
+def _list_job(job):
+    a, b, levels, mode = job
+    return ttc_pair(a, b, levels=levels, mode=mode)
+
+
+def ttc_pairs_list(pairs, levels: int, mode: int, workers: int):
+    """ttc_pair on every (E0, E1) host pair of `pairs` (frames of any sizes), spread over
+    `workers` spawned processes (workers <= 1: in this process); returns the list of
+    per-pair results in order and the seconds taken."""
+    import time
+
+    build()
+    jobs = [(a, b, levels, mode) for a, b in pairs]
+    t0 = time.perf_counter()
+    if workers <= 1:
+        out = [_list_job(j) for j in jobs]
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            out = pool.map(_list_job, jobs, chunksize=1)
+    return out, time.perf_counter() - t0
+

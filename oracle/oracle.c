@@ -31,7 +31,8 @@ enum { OR_FLAG_SINGULAR = 1, OR_FLAG_C_ZERO = 2, OR_FLAG_RECEDING = 4 };
 /* One result per pyramid level (mirrored by a numpy dtype in oracle/__init__.py). */
 typedef struct {
     double sums[10];     /* see oracle_sums for the order */
-    double abssums[10];  /* the same sums over |term| (error-bound scale) */
+    double abssums[10];  /* error-bound scale of each sum: sum of |term|, with G replaced
+                            by |x Ex| + |y Ey| in the four G terms (see oracle_sums) */
     double A, B, C;      /* Eq. final_TTC parameters, level-l pixel units */
     double ttc;          /* 1/C, frames */
     double x0, y0;       /* FOE, level-0 pixels from the principal point */
@@ -234,9 +235,14 @@ void oracle_sums(const double *Ex, const double *Ey, const double *Et, int h, in
             double G = x * ex + y * ey;
             double term[10] = { ex * ex, ex * ey, ey * ey, G * ex, G * ey, G * G,
                                 ex * et, ey * et, G * et, et * et };
+            /* magnitudes the rounding error of a finite-precision evaluation scales
+               with: G = x Ex + y Ey rounds relative to |x Ex| + |y Ey|, not to |G| */
+            double Gm = fabs(x * ex) + fabs(y * ey);
+            double mag[10] = { fabs(ex * ex), fabs(ex * ey), ey * ey, Gm * fabs(ex), Gm * fabs(ey), Gm * Gm,
+                               fabs(ex * et), fabs(ey * et), Gm * fabs(et), et * et };
             for (int s = 0; s < 10; ++s) {
                 csum_add(&acc[s], term[s]);
-                aacc[s] += fabs(term[s]);
+                aacc[s] += mag[s];
             }
         }
     for (int s = 0; s < 10; ++s) {

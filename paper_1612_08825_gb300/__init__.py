@@ -458,8 +458,12 @@ def ttc_solve_noalloc(prev: torch.Tensor, cur: torch.Tensor, levels: int = 1, mo
     H, W = prev.shape
     if out is None:
         out = torch.empty(levels * RESULT_DTYPE.itemsize, dtype=torch.uint8, device=prev.device)
-    _check(L.ttc_solve_noalloc(prev.data_ptr(), cur.data_ptr(), dt, H, W, prev.stride(0) * es, int(levels),
-                               int(mode), out.data_ptr(), _stream_ptr(prev)), "ttc_solve_noalloc")
+    if cur.device != prev.device or not out.is_cuda or out.device != prev.device:
+        raise ValueError("prev, cur and out must be on one CUDA device")
+    # the library uses the scratch array of the current device: make it prev's
+    with torch.cuda.device(prev.device):
+        _check(L.ttc_solve_noalloc(prev.data_ptr(), cur.data_ptr(), dt, H, W, prev.stride(0) * es, int(levels),
+                                   int(mode), out.data_ptr(), _stream_ptr(prev)), "ttc_solve_noalloc")
     return out
 
 

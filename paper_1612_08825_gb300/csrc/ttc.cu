@@ -1062,9 +1062,30 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[FT_NOALLOC_SCRATCH_BYT
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+void *g_noalloc_ctx[kMaxDevices] = {};    // the context that address belongs to
 
-// Device address of the scratch array on the current device (looked up once per
-// device; in host code the array's name is only a host-side stand-in).
+// cuCtxGetCurrent through the runtime's driver entry point (no libcuda link); null
+// when unavailable
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn ctx_get_current()
+{
+    static std::once_flag once;
+    static CtxGetCurrentFn fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(f);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// Device address of the scratch array on the current device (in host code the array's
+// name is only a host-side stand-in).  Looked up on the first call on a device and
+// again whenever that device's current context has changed (a context destroyed and
+// re-created reloads the module, which moves the array).
 ft_status noalloc_scratch(unsigned char **base)
 {
     int dev = 0;
@@ -1074,8 +1095,12 @@ ft_status noalloc_scratch(unsigned char **base)
         return FT_ERR_CUDA;
     }
     if (dev < 0 || dev >= kMaxDevices) return FT_ERR_UNSUPPORTED;
+    // null before the runtime has made the device's context current on this thread:
+    // the address is then looked up again on the next call
+    CUcontext cur = nullptr;
+    if (CtxGetCurrentFn get = ctx_get_current()) get(&cur);
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (!g_noalloc_addr[dev] || g_noalloc_ctx[dev] != static_cast<void *>(cur)) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) {
@@ -1083,6 +1108,7 @@ ft_status noalloc_scratch(unsigned char **base)
             return FT_ERR_CUDA;
         }
         g_noalloc_addr[dev] = ptr;
+        g_noalloc_ctx[dev] = cur;
     }
     *base = static_cast<unsigned char *>(g_noalloc_addr[dev]);
     return FT_OK;

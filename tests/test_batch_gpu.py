@@ -96,6 +96,44 @@ def test_batch_graph_replay():
     ctx.close()
 
 
+def _uneven_full_scale(n, seed):
+    """n pairs drawn like the 512-pair uneven workload (W 160-1920, H 120-1080, per-pair
+    depth and speed), with the first two forced to 1920 x 1080 and 160 x 120."""
+    specs = scenes.uneven_pair_sizes(n, seed=seed)
+    specs[0] = (1080, 1920) + specs[0][2:]
+    specs[1] = (120, 160) + specs[1][2:]
+    pairs, host = [], []
+    for i, (h, w, z0, sp) in enumerate(specs):
+        sc = scenes.tilted_plane_scene(H=h, W=w, seed=seed + 1000 + i, Z0=z0, speed=sp)
+        fr = scenes.render_sequence(sc, 2, device=DEV)
+        pairs.append((fr[0], fr[1]))
+        host.append((fr[0].cpu().numpy(), fr[1].cpu().numpy()))
+    return pairs, host
+
+
+@pytest.mark.parametrize("plan", ["autotuned", "forced"])
+def test_batch_full_scale_uneven_pairs_vs_oracle(plan):
+    """24 pairs of the uneven workload at full scale (up to 1920 x 1080), 5 levels, FOE:
+    every record against the FP64 oracle, under the autotuned tile plan and under the
+    plan 64, 64, 64, 64, 16 rows per level."""
+    levels = 5
+    pairs, host = _uneven_full_scale(24, seed=4242)
+    ctx = ft.TtcContext(1080, 1920, levels, len(pairs))
+    if plan == "forced":
+        ctx.batch_set_plan([64, 64, 64, 64, 16])
+    ctx.batch_prepare(pairs, levels=levels)
+    out = ctx.new_results(len(pairs) * levels)
+    if plan == "autotuned":
+        rows = ctx.batch_autotune(mode=1, reps=1, out=out)
+        assert all(r in (16, 64) for r in rows)
+    got = ft.results_to_numpy(ctx.batch_run(mode=1, out=out)).reshape(len(pairs), levels)
+    for i, (a, b) in enumerate(host):
+        ref = oracle.ttc_pair(a, b, levels=levels, mode=1)
+        for l in range(levels):
+            check_record(got[i, l], ref[l], 1, l)
+    ctx.close()
+
+
 def test_batch_errors():
     ctx = ft.TtcContext(100, 100, 2, 2)
     a = torch.zeros((100, 100), dtype=torch.uint8, device=DEV)

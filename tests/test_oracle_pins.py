@@ -236,6 +236,32 @@ def test_sums_exact_rational_uint8():
         assert abs(s[k] - float(exact[k])) <= 1e-15 * a[k] + 1e-300
 
 
+def test_sums_error_scale():
+    """abssums: the sum of |term| for the six plain products; for the four G terms the
+    rounding scale |x Ex| + |y Ey| replaces |G|, so it bounds |G| terms from above and
+    equals them when x Ex and y Ey never have opposite signs."""
+    rng = np.random.default_rng(5)
+    h, w = 9, 12
+    Ex, Ey, Et = (rng.standard_normal((h, w)) for _ in range(3))
+    cx, cy = 5.5, 4.0
+    s, a = oracle.sums(Ex, Ey, Et, cx, cy)
+    x = np.arange(w)[None, :] + 0.5 - cx
+    y = np.arange(h)[:, None] + 0.5 - cy
+    G = x * Ex + y * Ey
+    Gm = np.abs(x * Ex) + np.abs(y * Ey)
+    for k, t in ((0, Ex * Ex), (1, Ex * Ey), (2, Ey * Ey), (6, Ex * Et), (7, Ey * Et), (9, Et * Et)):
+        assert a[k] == pytest.approx(np.abs(t).sum(), rel=1e-13)
+    for k, g, e in ((3, G, Ex), (4, G, Ey), (5, G, G), (8, G, Et)):
+        assert a[k] >= np.abs(g * e).sum() * (1 - 1e-13)
+    assert a[5] == pytest.approx((Gm * Gm).sum(), rel=1e-13)
+    assert np.all(np.abs(s) <= a * (1 + 1e-13))
+    # Ey = 0: G = x Ex, so the scale is |G| itself
+    z = np.zeros_like(Ey)
+    s0, a0 = oracle.sums(Ex, z, Et, cx, cy)
+    assert a0[5] == pytest.approx(s0[5], rel=1e-13)
+    assert a0[3] == pytest.approx(np.abs(x * Ex * Ex).sum(), rel=1e-13)
+
+
 def test_solve_manufactured_Et_recovers_ABC():
     rng = np.random.default_rng(9)
     h, w = 40, 50

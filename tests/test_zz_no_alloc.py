@@ -1,4 +1,4 @@
-"""ttc_solve_noalloc against ttc_solve, through the C ABI.
+"""ttc_solve_noalloc against ttc_solve and the FP64 oracle, through the C ABI.
 
 ttc_solve_noalloc serves callers that must not allocate device memory once they are
 running (hard real-time loops, safety-certified software, plug-ins inside a process
@@ -13,8 +13,10 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_1612_08825_gb300 as ft
 import scenes
+from _tol import SUM_REL, SUM_REL_F32, check_record
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda")
@@ -32,24 +34,29 @@ def _close(got, ref):
             assert abs(g - r) <= REL * abs(r) + 1e-12, (k, g, r)
 
 
+@pytest.mark.parametrize("mode", [ft.MODE_TTC, ft.MODE_FOE])
 @pytest.mark.parametrize("H,W,levels,quantize", [(1080, 1920, 5, True), (150, 333, 4, True), (128, 128, 3, False)])
-def test_noalloc_matches_context_solve_on_two_calls(H, W, levels, quantize):
+def test_noalloc_matches_context_solve_and_oracle_on_two_calls(H, W, levels, quantize, mode):
     L = ft.load()
     sc = scenes.tilted_plane_scene(H=H, W=W, seed=H + W, quantize=quantize)
     fr = scenes.render_sequence(sc, 3, device=DEV)
+    host = fr.cpu().numpy().astype(np.float64)
     dt, es = (0, 1) if quantize else (1, 4)
+    rel = SUM_REL if quantize else SUM_REL_F32
     ctx = ft.TtcContext(H, W, levels, 1)
     stream = torch.cuda.current_stream().cuda_stream
     for t in range(2):                                   # two calls in a row, different pairs
         a, b = fr[t], fr[t + 1]
-        ref = ft.results_to_numpy(ctx.solve(a, b, levels=levels, mode=ft.MODE_FOE))
+        ref = ft.results_to_numpy(ctx.solve(a, b, levels=levels, mode=mode))
         out = torch.empty(levels * ft.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=DEV)
         st = L.ttc_solve_noalloc(a.data_ptr(), b.data_ptr(), dt, H, W, a.stride(0) * es, levels,
-                                 ft.MODE_FOE, out.data_ptr(), stream)
+                                 mode, out.data_ptr(), stream)
         assert st == 0, L.ft_status_string(st)
         got = ft.results_to_numpy(out)
+        orc = oracle.ttc_pair(host[t], host[t + 1], levels=levels, mode=mode)
         for l in range(levels):
             _close(got[l], ref[l])
+            check_record(got[l], orc[l], mode, l, rel=rel)
     ctx.close()
 
 
