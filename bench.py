@@ -251,11 +251,12 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
     for K in (9, 15, 21, 25, 31, 41, 51, 63):
         k = torch.from_numpy(scenes.normal_array((K, K), seed=K)).to(dev)
         out = ft.fastconv_nd(Ec, k)
-        ws = ft.fastconv_fft(Ec, k, out=torch.empty_like(out))._fastconv_workspace
+        plan = ft.FftPlan(tuple(Ec.shape), (K, K), dev)
+        ws = plan.new_workspace()
         t_dir, t_fft = [], []
         for i in range(reps + 2):
             for fn, acc in ((lambda: ft.fastconv_nd(Ec, k, out=out), t_dir),
-                            (lambda: ft.fastconv_fft(Ec, k, out=out, workspace=ws), t_fft)):
+                            (lambda: plan(Ec, k, out=out, workspace=ws), t_fft)):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)

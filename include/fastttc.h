@@ -100,26 +100,43 @@ ft_status fastconv_nd_typed(const void *input, int in_dtype, const int64_t *dims
  * Full convolution by FFT, for large kernels (Sec. IV-C, IV-D: above a kernel size
  * threshold the FFT method is faster, and FastConv switches to it).  Ranks 1-3.  Both
  * operands are zero-padded to FFT extents F_d >= N_d + K_d - 1 (products of 2, 3, 5, 7),
- * transformed real-to-complex (cuFFT; plans are created on first use of an extent and
- * cached per device), multiplied pointwise, transformed back and cropped to out.
+ * transformed real-to-complex (cuFFT), multiplied pointwise, transformed back and
+ * cropped to out.
  * Error: normwise, about FP32 rounding times log2(prod F) times ||input||_2 ||kernel||_2
  * per element, unlike the per-element bound of the direct path.
- *   workspace: device, at least fastconv_fft_workspace() bytes.
- * Calls from several host threads or streams are serialised on a process-wide lock
- * while they enqueue the transforms.
- * Errors: FT_ERR_INVALID_ARG, FT_ERR_SHAPE (as fastconv_nd), FT_ERR_UNSUPPORTED (rank > 3,
- * more than 2^30 output values), FT_ERR_WORKSPACE, FT_ERR_CUDA (also for cuFFT errors).
+ *
+ * fastconv_fft_plan_create: the transforms for input dims and kernel kdims (host
+ *   arrays, as fastconv_nd) on the current device.  This is the call that allocates
+ *   (cuFFT's plan data): make it once per shape, before any timed loop or stream
+ *   capture.  *workspace_bytes (nullable) receives the bytes a call needs: the padded
+ *   operands, their spectra and cuFFT's work area.  The plan is owned by the caller
+ *   until fastconv_fft_plan_destroy.  Errors: FT_ERR_INVALID_ARG, FT_ERR_SHAPE,
+ *   FT_ERR_UNSUPPORTED (rank > 3, more than 2^30 output values), FT_ERR_CUDA.
+ * fastconv_fft: one convolution with a plan; allocates nothing and does not
+ *   synchronise.  workspace: device, 256-byte aligned, at least
+ *   fastconv_fft_plan_workspace(plan) bytes, owned by this call until the stream has
+ *   passed it (calls on different streams need different workspaces; one plan serves
+ *   them all, the binding of a stream and work area to it is serialised per plan).
+ *   The current device must be the plan's.  Errors: FT_ERR_INVALID_ARG,
+ *   FT_ERR_WORKSPACE, FT_ERR_CUDA (also for cuFFT errors).
  */
-ft_status fastconv_fft_workspace(const int64_t *dims, int nd, const int64_t *kdims, size_t *bytes);
-ft_status fastconv_fft(const float *input, const int64_t *dims, int nd, const float *kernel, const int64_t *kdims,
-                       float *out, void *workspace, size_t workspace_bytes, void *stream);
+typedef struct fastconv_fft_plan fastconv_fft_plan;
+ft_status fastconv_fft_plan_create(const int64_t *dims, int nd, const int64_t *kdims, fastconv_fft_plan **plan,
+                                   size_t *workspace_bytes);
+void fastconv_fft_plan_destroy(fastconv_fft_plan *plan);
+size_t fastconv_fft_plan_workspace(const fastconv_fft_plan *plan);
+ft_status fastconv_fft(fastconv_fft_plan *plan, const float *input, const float *kernel, float *out,
+                       void *workspace, size_t workspace_bytes, void *stream);
 
 /*
  * Host only: 1 when the FFT path is expected to be faster than the direct path for
- * this request (kernels of at least FT_FFT_MIN_TAPS taps, rank <= 3), 0 otherwise.
- * FT_FFT_MIN_TAPS is the crossover measured on GB300 for 1080 x 1920 images.
+ * this request, 0 otherwise: 2-D requests whose kernel has at least FT_FFT_MIN_TAPS
+ * taps and whose output has at least FT_FFT_MIN_OUTPUT values.  The crossover was
+ * measured on GB300 for 1080 x 1920 images only; 3-D kernels and small images keep the
+ * direct path (and its per-element error bound).
  */
-#define FT_FFT_MIN_TAPS 961    /* 31 x 31: direct 86 us at 25 x 25 and 117 us at 31 x 31, FFT 109 us */
+#define FT_FFT_MIN_TAPS 961          /* 31 x 31: direct 86 us at 25 x 25 and 117 us at 31 x 31, FFT 109 us */
+#define FT_FFT_MIN_OUTPUT 1000000    /* output values: about a 1080 x 1920 image */
 int fastconv_prefers_fft(const int64_t *dims, int nd, const int64_t *kdims);
 
 /*
@@ -333,13 +350,24 @@ ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_t frame_str
  *           must stay valid and unchanged until `stream` reaches the end of the call.
  *   out:    host, (T-1) * levels records (page-locked for an asynchronous copy), valid
  *           once `stream` has reached the end of the call.
- * The first call (and a call needing larger buffers) allocates the buffers, the copy
- * streams and their events in the context (freed by ttc_ctx_destroy); a call that
- * grows them synchronises the device first.  Calls on one context must be ordered
- * (one stream).  Errors: as ttc_solve_sequence, FT_ERR_SHAPE (frame stride shorter than
- * a frame), FT_ERR_CUDA.
+ * The call allocates nothing: the two device buffers and the records buffer are sized
+ * beforehand by ttc_ctx_reserve_host for at least this request (same frame stride, T,
+ * dtype, H, W, pitch and levels, or smaller), the copy streams and their events are
+ * made by ttc_ctx_create.  Successive calls on one context may use different streams:
+ * a call's uploads wait until the previous call has finished with the buffers.
+ * Errors: as ttc_solve_sequence, FT_ERR_SHAPE (frame stride shorter than a frame),
+ * FT_ERR_WORKSPACE (buffers not reserved for this request), FT_ERR_CUDA.
+ *
+ * ttc_ctx_reserve_host: sizes the context's host-sequence buffers for requests up to
+ * the given one (the same arguments as ttc_solve_sequence_host); allocates only when
+ * they must grow, and then first waits (on the host) for this context's last
+ * host-sequence call to finish with them -- no device-wide synchronisation, so other
+ * streams and contexts keep running.  Freed by ttc_ctx_destroy.  Errors: FT_ERR_INVALID_ARG,
+ * FT_ERR_SHAPE, FT_ERR_WORKSPACE (larger than the context), FT_ERR_CUDA.
  */
 #define FT_SEQ_CHUNK_PAIRS 64
+ft_status ttc_ctx_reserve_host(ttc_ctx *ctx, int64_t frame_stride_bytes, int T, int dtype, int H, int W,
+                               int64_t pitch_bytes, int levels);
 ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
                                   int dtype, int H, int W, int64_t pitch_bytes, int levels, int mode,
                                   ttc_level_result *out, void *stream);

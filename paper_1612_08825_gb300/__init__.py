@@ -20,7 +20,8 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "fastconv_check", "fastconv_separable", "fastconv_fft", "fastconv",
+    "FtError", "lib", "load", "fastconv_out_dims", "fastconv_nd", "fastconv_check", "fastconv_separable", "fastconv_fft",
+    "FftPlan", "fastconv",
     "factor_kernel", "ttc_derivatives", "gradient",
     "ttc_solve_noalloc",
     "TtcContext", "RESULT_DTYPE", "results_to_numpy", "select_level",
@@ -97,9 +98,14 @@ def load(path: Optional[str] = None):
     L.fastconv_nd.restype = st
     L.fastconv_nd_typed.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_int, _vp, _i64p, _vp, _vp, _vp]
     L.fastconv_nd_typed.restype = st
-    L.fastconv_fft_workspace.argtypes = [_i64p, ctypes.c_int, _i64p, ctypes.POINTER(ctypes.c_size_t)]
-    L.fastconv_fft_workspace.restype = st
-    L.fastconv_fft.argtypes = [_vp, _i64p, ctypes.c_int, _vp, _i64p, _vp, _vp, ctypes.c_size_t, _vp]
+    L.fastconv_fft_plan_create.argtypes = [_i64p, ctypes.c_int, _i64p, ctypes.POINTER(_vp),
+                                           ctypes.POINTER(ctypes.c_size_t)]
+    L.fastconv_fft_plan_create.restype = st
+    L.fastconv_fft_plan_destroy.argtypes = [_vp]
+    L.fastconv_fft_plan_destroy.restype = None
+    L.fastconv_fft_plan_workspace.argtypes = [_vp]
+    L.fastconv_fft_plan_workspace.restype = ctypes.c_size_t
+    L.fastconv_fft.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
     L.fastconv_fft.restype = st
     L.fastconv_prefers_fft.argtypes = [_i64p, ctypes.c_int, _i64p]
     L.fastconv_prefers_fft.restype = ctypes.c_int
@@ -137,6 +143,9 @@ def load(path: Optional[str] = None):
     L.ttc_solve_sequence.restype = st
     L.ttc_solve_sequence_host.argtypes = L.ttc_solve_sequence.argtypes
     L.ttc_solve_sequence_host.restype = st
+    L.ttc_ctx_reserve_host.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int64, ctypes.c_int]
+    L.ttc_ctx_reserve_host.restype = st
     L.ttc_partial_sums.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int64, ctypes.c_int, _vp]
     L.ttc_partial_sums.restype = st
@@ -264,28 +273,81 @@ def fastconv_nd(x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = 
     return out
 
 
+class FftPlan:
+    """cuFFT transforms for one (input shape, kernel shape) on one device
+    (fastconv_fft_plan_create: the call that allocates); calls with it allocate nothing
+    but the workspace the caller passes or that the plan keeps for the default stream."""
+
+    def __init__(self, shape, kshape, device=None):
+        L = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.shape, self.kshape = tuple(int(v) for v in shape), tuple(int(v) for v in kshape)
+        if len(self.shape) != len(self.kshape):
+            raise ValueError("shape and kshape must have the same rank")
+        h = _vp()
+        nbytes = ctypes.c_size_t(0)
+        with torch.cuda.device(self.device):
+            _check(L.fastconv_fft_plan_create(_dims(self.shape), len(self.shape), _dims(self.kshape), ctypes.byref(h),
+                                              ctypes.byref(nbytes)), "fastconv_fft_plan_create")
+        self._h = h
+        self.workspace_bytes = int(nbytes.value)
+
+    def new_workspace(self) -> torch.Tensor:
+        return torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+
+    def __call__(self, x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = None,
+                 workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        L = load()
+        _require_cuda(x, "x")
+        _require_cuda(k, "k")
+        if x.dtype != torch.float32 or k.dtype != torch.float32:
+            raise ValueError("float32 tensors")
+        if tuple(x.shape) != self.shape or tuple(k.shape) != self.kshape or x.device != self.device:
+            raise ValueError("x and k do not match the plan")
+        x = x.contiguous()
+        k = k.contiguous()
+        od = tuple(n + m - 1 for n, m in zip(self.shape, self.kshape))
+        out = torch.empty(od, dtype=torch.float32, device=x.device) if out is None else out
+        if tuple(out.shape) != od or not out.is_contiguous() or out.dtype != torch.float32:
+            raise ValueError("out has the wrong shape, dtype or layout")
+        if workspace is None:
+            workspace = self.new_workspace()
+        with torch.cuda.device(self.device):
+            _check(L.fastconv_fft(self._h, x.data_ptr(), k.data_ptr(), out.data_ptr(), workspace.data_ptr(),
+                                  workspace.numel() * workspace.element_size(), _stream_ptr(x)), "fastconv_fft")
+        out._fastconv_workspace = workspace        # alive until the caller drops `out`
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().fastconv_fft_plan_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_fft_plans = {}
+
+
 def fastconv_fft(x: torch.Tensor, k: torch.Tensor, out: Optional[torch.Tensor] = None,
                  workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Full convolution by FFT (ranks 1-3, float32), for large kernels."""
-    L = load()
+    """Full convolution by FFT (ranks 1-3, float32), for large kernels.  Keeps one
+    FftPlan per (device, shapes) in this module: the first call of a shape creates it."""
     _require_cuda(x, "x")
     _require_cuda(k, "k")
     if x.dtype != torch.float32 or k.dtype != torch.float32 or x.dim() != k.dim():
         raise ValueError("float32 tensors of one rank")
-    x = x.contiguous()
-    k = k.contiguous()
-    nbytes = ctypes.c_size_t(0)
-    _check(L.fastconv_fft_workspace(_dims(x.shape), x.dim(), _dims(k.shape), ctypes.byref(nbytes)),
-           "fastconv_fft_workspace")
-    if workspace is None or workspace.numel() * workspace.element_size() < nbytes.value:
-        workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=x.device)
-    od = fastconv_out_dims(x.shape, k.shape)
-    out = torch.empty(od, dtype=torch.float32, device=x.device) if out is None else out
-    _check(L.fastconv_fft(x.data_ptr(), _dims(x.shape), x.dim(), k.data_ptr(), _dims(k.shape), out.data_ptr(),
-                          workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(x)),
-           "fastconv_fft")
-    out._fastconv_workspace = workspace
-    return out
+    key = (x.device, tuple(x.shape), tuple(k.shape))
+    plan = _fft_plans.get(key)
+    if plan is None:
+        plan = _fft_plans[key] = FftPlan(x.shape, k.shape, x.device)
+    if workspace is not None and workspace.numel() * workspace.element_size() < plan.workspace_bytes:
+        workspace = None
+    return plan(x, k, out=out, workspace=workspace)
 
 
 def fastconv(x: torch.Tensor, k: torch.Tensor, method: str = "auto") -> torch.Tensor:
@@ -553,6 +615,7 @@ class TtcContext:
             elif out.is_cuda or out.numel() * out.element_size() < n * RESULT_DTYPE.itemsize:
                 raise ValueError("out must be a host tensor of (T-1) * levels records")
             stream = torch.cuda.current_stream(self.device).cuda_stream
+            self.reserve_host(frames, levels)
             _check(L.ttc_solve_sequence_host(self._h, frames.data_ptr(), frames.stride(0) * es, T, dt, H, W,
                                              frames.stride(1) * es, int(levels), int(mode), out.data_ptr(), stream),
                    "ttc_solve_sequence_host")
@@ -563,6 +626,15 @@ class TtcContext:
                                     frames.stride(1) * es, int(levels), int(mode), out.data_ptr(),
                                     _stream_ptr(frames)), "ttc_solve_sequence")
         return out
+
+    def reserve_host(self, frames: torch.Tensor, levels: int = 1):
+        """Size the context's host-sequence buffers for `frames` (T, H, W) on the host
+        (ttc_ctx_reserve_host: allocates only when they must grow)."""
+        L = load()
+        dt, es, T, H, W = self._seq_args(frames)
+        with torch.cuda.device(self.device):
+            _check(L.ttc_ctx_reserve_host(self._h, frames.stride(0) * es, T, dt, H, W, frames.stride(1) * es,
+                                          int(levels)), "ttc_ctx_reserve_host")
 
     @staticmethod
     def host_upload_bytes(T: int, frame_bytes: int, max_pairs: int) -> int:

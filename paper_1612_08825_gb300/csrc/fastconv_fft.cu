@@ -5,14 +5,15 @@
 // FFT sizes F >= M (products of 2, 3, 5 and 7), transformed real-to-complex with
 // cuFFT, multiplied pointwise (with the 1 / prod(F) of the inverse), transformed back,
 // and the M-extent corner is copied to the output.  Padding, the product and the crop
-// are this file's kernels; the transforms are cuFFT's, with plans cached per shape.
+// are this file's kernels; the transforms are cuFFT's.  The plans belong to an explicit
+// plan object (fastconv_fft_plan_create): they are made without an internal work area,
+// and each call binds the work area inside the caller's workspace, so calls allocate
+// nothing and calls on different streams never share scratch memory.
 #include <cufft.h>
 
 #include <algorithm>
-
-#include <map>
 #include <mutex>
-#include <vector>
+#include <new>
 
 #include "common.cuh"
 
@@ -50,39 +51,6 @@ Shape fft_shape(const int64_t *dims, int nd, const int64_t *kdims)
         sh.C *= d + 1 < nd ? sh.F[d] : sh.F[d] / 2 + 1;
     }
     return sh;
-}
-
-struct Plans {
-    cufftHandle fwd, inv;
-};
-
-std::mutex g_mu;
-std::map<std::vector<int64_t>, Plans> g_plans;   // key: device, F[0..nd-1]
-
-cufftResult get_plans(const Shape &sh, Plans *out)
-{
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::vector<int64_t> key{dev};
-    for (int d = 0; d < sh.nd; ++d) key.push_back(sh.F[d]);
-    auto it = g_plans.find(key);
-    if (it != g_plans.end()) {
-        *out = it->second;
-        return CUFFT_SUCCESS;
-    }
-    int n[3];
-    for (int d = 0; d < sh.nd; ++d) n[d] = (int)sh.F[d];
-    Plans p{};
-    cufftResult r = cufftPlanMany(&p.fwd, sh.nd, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1);
-    if (r != CUFFT_SUCCESS) return r;
-    r = cufftPlanMany(&p.inv, sh.nd, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1);
-    if (r != CUFFT_SUCCESS) {
-        cufftDestroy(p.fwd);
-        return r;
-    }
-    g_plans[key] = p;
-    *out = p;
-    return CUFFT_SUCCESS;
 }
 
 struct Ext {
@@ -180,61 +148,144 @@ ft_status check_args(const int64_t *dims, int nd, const int64_t *kdims)
 
 }  // namespace
 
-extern "C" ft_status fastconv_fft_workspace(const int64_t *dims, int nd, const int64_t *kdims, size_t *bytes)
+struct fastconv_fft_plan {
+    int dev;                  // the device the cuFFT plans were made on
+    int nd;
+    int64_t dims[3], kdims[3];
+    Shape sh;
+    cufftHandle fwd, inv;
+    size_t pad_bytes;         // the two real and two complex arrays
+    size_t work_bytes;        // cuFFT's work area (shared by the forward and inverse plans)
+    std::mutex mu;            // serialises binding stream and work area + enqueueing
+};
+
+namespace {
+
+// bytes of the padded real arrays and the complex spectra, each 256-byte aligned
+void pad_sizes(const Shape &sh, size_t *r, size_t *c)
 {
-    if (!bytes) return FT_ERR_INVALID_ARG;
+    *r = ((size_t)sh.R * sizeof(float) + 255) / 256 * 256;
+    *c = ((size_t)sh.C * sizeof(cufftComplex) + 255) / 256 * 256;
+}
+
+}  // namespace
+
+extern "C" ft_status fastconv_fft_plan_create(const int64_t *dims, int nd, const int64_t *kdims,
+                                              fastconv_fft_plan **plan, size_t *workspace_bytes)
+{
+    if (!plan) return FT_ERR_INVALID_ARG;
+    *plan = nullptr;
     const ft_status st = check_args(dims, nd, kdims);
     if (st != FT_OK) return st;
-    const Shape sh = fft_shape(dims, nd, kdims);
-    // two real arrays and two complex arrays, each 256-byte aligned
-    const size_t r = ((size_t)sh.R * sizeof(float) + 255) / 256 * 256;
-    const size_t c = ((size_t)sh.C * sizeof(cufftComplex) + 255) / 256 * 256;
-    *bytes = 2 * r + 2 * c;
+    fastconv_fft_plan *p = new (std::nothrow) fastconv_fft_plan();
+    if (!p) return FT_ERR_CUDA;
+    cudaError_t e = cudaGetDevice(&p->dev);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        delete p;
+        return FT_ERR_CUDA;
+    }
+    p->nd = nd;
+    for (int d = 0; d < nd; ++d) {
+        p->dims[d] = dims[d];
+        p->kdims[d] = kdims[d];
+    }
+    p->sh = fft_shape(dims, nd, kdims);
+    int n[3];
+    for (int d = 0; d < nd; ++d) n[d] = (int)p->sh.F[d];
+    size_t wf = 0, wi = 0;
+    bool made_f = false, made_i = false;
+    cufftResult r = cufftCreate(&p->fwd);
+    if (r == CUFFT_SUCCESS) {
+        made_f = true;
+        r = cufftSetAutoAllocation(p->fwd, 0);
+    }
+    if (r == CUFFT_SUCCESS) r = cufftMakePlanMany(p->fwd, nd, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, &wf);
+    if (r == CUFFT_SUCCESS) r = cufftCreate(&p->inv);
+    if (r == CUFFT_SUCCESS) {
+        made_i = true;
+        r = cufftSetAutoAllocation(p->inv, 0);
+    }
+    if (r == CUFFT_SUCCESS) r = cufftMakePlanMany(p->inv, nd, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1, &wi);
+    if (r != CUFFT_SUCCESS) {
+        if (made_f) cufftDestroy(p->fwd);
+        if (made_i) cufftDestroy(p->inv);
+        delete p;
+        ft::set_cuda_error(cudaErrorUnknown);
+        return FT_ERR_CUDA;
+    }
+    size_t rb, cb;
+    pad_sizes(p->sh, &rb, &cb);
+    p->pad_bytes = 2 * rb + 2 * cb;
+    p->work_bytes = (std::max(wf, wi) + 255) / 256 * 256;
+    if (workspace_bytes) *workspace_bytes = p->pad_bytes + p->work_bytes;
+    *plan = p;
     return FT_OK;
 }
 
-extern "C" ft_status fastconv_fft(const float *input, const int64_t *dims, int nd, const float *kernel,
-                                  const int64_t *kdims, float *out, void *workspace, size_t workspace_bytes,
-                                  void *stream)
+extern "C" void fastconv_fft_plan_destroy(fastconv_fft_plan *plan)
 {
-    if (!input || !kernel || !out || !workspace) return FT_ERR_INVALID_ARG;
-    ft_status st = check_args(dims, nd, kdims);
-    if (st != FT_OK) return st;
-    size_t need = 0;
-    fastconv_fft_workspace(dims, nd, kdims, &need);
-    if (workspace_bytes < need) return FT_ERR_WORKSPACE;
-    const Shape sh = fft_shape(dims, nd, kdims);
-    const size_t r = ((size_t)sh.R * sizeof(float) + 255) / 256 * 256;
-    const size_t c = ((size_t)sh.C * sizeof(cufftComplex) + 255) / 256 * 256;
+    if (!plan) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != plan->dev) cudaSetDevice(plan->dev);
+    cufftDestroy(plan->fwd);
+    cufftDestroy(plan->inv);
+    if (cur != plan->dev) cudaSetDevice(cur);
+    delete plan;
+}
+
+extern "C" size_t fastconv_fft_plan_workspace(const fastconv_fft_plan *plan)
+{
+    return plan ? plan->pad_bytes + plan->work_bytes : 0;
+}
+
+extern "C" ft_status fastconv_fft(fastconv_fft_plan *plan, const float *input, const float *kernel, float *out,
+                                  void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!plan || !input || !kernel || !out || !workspace) return FT_ERR_INVALID_ARG;
+    if (workspace_bytes < plan->pad_bytes + plan->work_bytes) return FT_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return FT_ERR_INVALID_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    if (dev != plan->dev) return FT_ERR_INVALID_ARG;
+    const int nd = plan->nd;
+    const Shape &sh = plan->sh;
+    size_t r, c;
+    pad_sizes(sh, &r, &c);
     unsigned char *w = static_cast<unsigned char *>(workspace);
     float *ra = reinterpret_cast<float *>(w), *rb = reinterpret_cast<float *>(w + r);
     cufftComplex *ca = reinterpret_cast<cufftComplex *>(w + 2 * r);
     cufftComplex *cb = reinterpret_cast<cufftComplex *>(w + 2 * r + c);
+    void *work = w + plan->pad_bytes;
     int64_t m[3];
-    int64_t mtot = 1;
-    for (int d = 0; d < nd; ++d) {
-        m[d] = dims[d] + kdims[d] - 1;
-        mtot *= m[d];
-    }
+    for (int d = 0; d < nd; ++d) m[d] = plan->dims[d] + plan->kdims[d] - 1;
     cudaStream_t s = ft::as_stream(stream);
     const Ext F = ext3(sh.F, nd);
     const dim3 pg = row_grid(F.a[0] * F.a[1], F.a[2]);
-    pad_kernel<<<pg, kThreads, 0, s>>>(input, ext3(dims, nd), F, ra);
-    pad_kernel<<<pg, kThreads, 0, s>>>(kernel, ext3(kdims, nd), F, rb);
-    if ((st = ft::check_launch()) != FT_OK) return st;
+    pad_kernel<<<pg, kThreads, 0, s>>>(input, ext3(plan->dims, nd), F, ra);
+    pad_kernel<<<pg, kThreads, 0, s>>>(kernel, ext3(plan->kdims, nd), F, rb);
+    ft_status st = ft::check_launch();
+    if (st != FT_OK) return st;
     {
-        std::lock_guard<std::mutex> lock(g_mu);
-        Plans p;
-        cufftResult fr = get_plans(sh, &p);
-        if (fr == CUFFT_SUCCESS) fr = cufftSetStream(p.fwd, s);
-        if (fr == CUFFT_SUCCESS) fr = cufftSetStream(p.inv, s);
-        if (fr == CUFFT_SUCCESS) fr = cufftExecR2C(p.fwd, ra, ca);
-        if (fr == CUFFT_SUCCESS) fr = cufftExecR2C(p.fwd, rb, cb);
+        // the plans' stream and work area are bound per call; the lock keeps another
+        // thread from rebinding them between this call's bind and its enqueue
+        std::lock_guard<std::mutex> lock(plan->mu);
+        cufftResult fr = cufftSetStream(plan->fwd, s);
+        if (fr == CUFFT_SUCCESS) fr = cufftSetWorkArea(plan->fwd, work);
+        if (fr == CUFFT_SUCCESS) fr = cufftExecR2C(plan->fwd, ra, ca);
+        if (fr == CUFFT_SUCCESS) fr = cufftExecR2C(plan->fwd, rb, cb);
         if (fr == CUFFT_SUCCESS) {
             mul_kernel<<<grid_for(sh.C), kThreads, 0, s>>>(ca, cb, sh.C, (float)(1.0 / (double)sh.R));
             if ((st = ft::check_launch()) != FT_OK) return st;
-            fr = cufftExecC2R(p.inv, ca, ra);
+            fr = cufftSetStream(plan->inv, s);
         }
+        if (fr == CUFFT_SUCCESS) fr = cufftSetWorkArea(plan->inv, work);
+        if (fr == CUFFT_SUCCESS) fr = cufftExecC2R(plan->inv, ca, ra);
         if (fr != CUFFT_SUCCESS) {
             ft::set_cuda_error(cudaErrorUnknown);
             return FT_ERR_CUDA;
@@ -245,12 +296,14 @@ extern "C" ft_status fastconv_fft(const float *input, const int64_t *dims, int n
     return ft::check_launch();
 }
 
-// The kernel size above which the FFT path is faster on this part (measured with the
-// bench's crossover sweep on 1080 x 1920 images: see FT_FFT_MIN_TAPS in the header).
+// The switch to the FFT path: measured on GB300 for 2-D 1080 x 1920 images (the
+// crossover sweep of the bench), so only 2-D requests of at least that output area
+// with at least FT_FFT_MIN_TAPS taps take it; 3-D kernels and small images, whose
+// crossover was not measured, stay on the direct path (with its per-element bound).
 extern "C" int fastconv_prefers_fft(const int64_t *dims, int nd, const int64_t *kdims)
 {
-    if (check_args(dims, nd, kdims) != FT_OK) return 0;
-    int64_t taps = 1;
-    for (int d = 0; d < nd; ++d) taps *= kdims[d];
-    return taps >= FT_FFT_MIN_TAPS ? 1 : 0;
+    if (check_args(dims, nd, kdims) != FT_OK || nd != 2) return 0;
+    const int64_t taps = kdims[0] * kdims[1];
+    const int64_t area = (dims[0] + kdims[0] - 1) * (dims[1] + kdims[1] - 1);
+    return taps >= FT_FFT_MIN_TAPS && area >= FT_FFT_MIN_OUTPUT ? 1 : 0;
 }

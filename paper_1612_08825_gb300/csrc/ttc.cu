@@ -422,7 +422,9 @@ struct ttc_ctx {
     size_t ring_out_records;
     cudaStream_t cstream[2];
     cudaEvent_t ev_start, ev_copied[2], ev_free[2];
-    bool ring_ready;
+    cudaEvent_t ev_ring_done;         // the last host-sequence call has finished with the ring
+    bool ring_ready;                  // streams and events exist
+    bool ring_used;                   // ev_ring_done has been recorded
 };
 
 extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max_levels, int max_pairs)
@@ -490,11 +492,27 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
         delete c;
         return FT_ERR_CUDA;
     }
+    // copy streams and events of host-frame sequences (no device memory: the ring
+    // itself is sized by ttc_ctx_reserve_host)
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaStreamCreateWithFlags(&c->cstream[b], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_copied[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_free[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_ring_done, cudaEventDisableTiming);
+    c->ring_ready = e == cudaSuccess;
+    if (e != cudaSuccess) ft::set_cuda_error(e);
     c->d_descs = reinterpret_cast<ttc_pass::PassParams *>(dbuf);
     c->d_prefix = reinterpret_cast<int *>(dbuf + b_desc);
     c->d_sdesc = reinterpret_cast<SolveDesc *>(dbuf + b_desc + b_pre);
     c->bytes += c->stage_bytes;
     *ctx = c;
+    if (!c->ring_ready) {
+        ttc_ctx_destroy(c);
+        *ctx = nullptr;
+        return FT_ERR_CUDA;
+    }
     return FT_OK;
 }
 
@@ -507,18 +525,19 @@ extern "C" void ttc_ctx_destroy(ttc_ctx *ctx)
     cudaFree(ctx->d_descs);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
-    if (ctx->ring_ready) {
-        cudaStreamSynchronize(ctx->cstream[0]);
-        cudaStreamSynchronize(ctx->cstream[1]);
-        for (int b = 0; b < 2; ++b) {
+    if (ctx->ring_used) cudaEventSynchronize(ctx->ev_ring_done);
+    for (int b = 0; b < 2; ++b) {
+        if (ctx->cstream[b]) {
+            cudaStreamSynchronize(ctx->cstream[b]);
             cudaStreamDestroy(ctx->cstream[b]);
-            cudaEventDestroy(ctx->ev_copied[b]);
-            cudaEventDestroy(ctx->ev_free[b]);
         }
-        cudaEventDestroy(ctx->ev_start);
+        if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);
+        if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
     }
-    cudaFree(ctx->ring);
-    cudaFree(ctx->ring_out);
+    if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    if (ctx->ev_ring_done) cudaEventDestroy(ctx->ev_ring_done);
+    if (ctx->ring) cudaFree(ctx->ring);
+    if (ctx->ring_out) cudaFree(ctx->ring_out);
     delete[] ctx->h_pairs;
     delete ctx;
 }
@@ -1163,56 +1182,21 @@ extern "C" ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_
 
 namespace {
 
-// the ring, results buffer, copy streams and events of host-frame sequences
-ft_status ring_setup(ttc_ctx *ctx, size_t bytes, size_t records)
-{
-    cudaError_t e = cudaSuccess;
-    if (!ctx->ring_ready) {
-        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-            e = cudaStreamCreateWithFlags(&ctx->cstream[b], cudaStreamNonBlocking);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming);
-        }
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            ft::set_cuda_error(e);
-            return FT_ERR_CUDA;
-        }
-        ctx->ring_ready = true;
-    }
-    if (bytes > ctx->ring_bytes || records > ctx->ring_out_records) {
-        // the buffers may still be in use by an earlier call
-        e = cudaDeviceSynchronize();
-        if (e == cudaSuccess && bytes > ctx->ring_bytes) {
-            cudaFree(ctx->ring);
-            ctx->ring = nullptr;
-            ctx->ring_bytes = 0;
-            e = cudaMalloc(&ctx->ring, 2 * bytes);
-            if (e == cudaSuccess) ctx->ring_bytes = bytes;
-        }
-        if (e == cudaSuccess && records > ctx->ring_out_records) {
-            cudaFree(ctx->ring_out);
-            ctx->ring_out = nullptr;
-            ctx->ring_out_records = 0;
-            e = cudaMalloc(&ctx->ring_out, records * sizeof(ttc_level_result));
-            if (e == cudaSuccess) ctx->ring_out_records = records;
-        }
-        if (e != cudaSuccess) {
-            ft::set_cuda_error(e);
-            return FT_ERR_CUDA;
-        }
-    }
-    return FT_OK;
-}
+// Ring and records sizes a host-frame sequence needs.  Float frames: a frame's pyramid
+// images are rounded differently when written as the first frame of a pair (block sums
+// of its pixels) and as the second (first frame's sums plus the sums of the
+// differences), and the level-l image of a second frame depends on the level-(l-1)
+// image of the frame before it.  So that every record equals the whole-sequence call,
+// a chunk after the first also computes the levels - 1 pairs before it (their records
+// are not written).  uint8 sums are exact either way.
+struct HostPlan {
+    int lead, chunk, nchunks;
+    size_t frame_bytes, buf_bytes, records;
+};
 
-}  // namespace
-
-extern "C" ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
-                                             int dtype, int H, int W, int64_t pitch_bytes, int levels, int mode,
-                                             ttc_level_result *out, void *stream)
+ft_status host_plan(const ttc_ctx *ctx, int64_t frame_stride_bytes, int T, int dtype, int H, int W,
+                    int64_t pitch_bytes, int levels, HostPlan *hp)
 {
-    if (!ctx || !frames || !out) return FT_ERR_INVALID_ARG;
-    if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
     if (T < 2) return FT_ERR_SHAPE;
     ft_status st = check_frames(dtype, H, W, pitch_bytes);
     if (st != FT_OK) return st;
@@ -1220,20 +1204,79 @@ extern "C" ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, i
     if (frame_stride_bytes < pitch_bytes * (H - 1) + (int64_t)W * elem_size(dtype)) return FT_ERR_SHAPE;
     if (H > ctx->max_H || W > ctx->max_W || levels > ctx->max_levels) return FT_ERR_WORKSPACE;
     const int npairs = T - 1;
-    // Float frames: a frame's pyramid images are rounded differently when written as
-    // the first frame of a pair (block sums of its pixels) and as the second (first
-    // frame's sums plus the sums of the differences), and the level-l image of a second
-    // frame depends on the level-(l-1) image of the frame before it.  So that every
-    // record equals the whole-sequence call, a chunk after the first also computes the
-    // levels - 1 pairs before it (their records are not written).  uint8 sums are exact
-    // either way.
-    const int lead = (dtype == FT_F32 && ctx->max_pairs > levels - 1) ? levels - 1 : 0;
-    const int chunk = std::min(std::min(FT_SEQ_CHUNK_PAIRS, ctx->max_pairs - lead), npairs);
-    const int nchunks = (npairs + chunk - 1) / chunk;
-    const size_t frame_bytes = (size_t)(pitch_bytes * (H - 1) + (int64_t)W * elem_size(dtype));
-    const size_t buf_bytes =
-        ((size_t)(chunk + lead) * (size_t)frame_stride_bytes + frame_bytes + 255) / 256 * 256;
-    if ((st = ring_setup(ctx, buf_bytes, (size_t)npairs * levels)) != FT_OK) return st;
+    hp->lead = (dtype == FT_F32 && ctx->max_pairs > levels - 1) ? levels - 1 : 0;
+    hp->chunk = std::min(std::min(FT_SEQ_CHUNK_PAIRS, ctx->max_pairs - hp->lead), npairs);
+    hp->nchunks = (npairs + hp->chunk - 1) / hp->chunk;
+    hp->frame_bytes = (size_t)(pitch_bytes * (H - 1) + (int64_t)W * elem_size(dtype));
+    hp->buf_bytes = ((size_t)(hp->chunk + hp->lead) * (size_t)frame_stride_bytes + hp->frame_bytes + 255) / 256 * 256;
+    hp->records = (size_t)npairs * levels;
+    return FT_OK;
+}
+
+}  // namespace
+
+extern "C" ft_status ttc_ctx_reserve_host(ttc_ctx *ctx, int64_t frame_stride_bytes, int T, int dtype, int H, int W,
+                                          int64_t pitch_bytes, int levels)
+{
+    if (!ctx) return FT_ERR_INVALID_ARG;
+    if (!ctx->ring_ready) return FT_ERR_CUDA;
+    HostPlan hp;
+    ft_status st = host_plan(ctx, frame_stride_bytes, T, dtype, H, W, pitch_bytes, levels, &hp);
+    if (st != FT_OK) return st;
+    if (hp.buf_bytes <= ctx->ring_bytes && hp.records <= ctx->ring_out_records) return FT_OK;
+    // the buffers may still be in use by this context's last host-sequence call: wait for
+    // that call only, then free and allocate in stream order on the context's first copy
+    // stream (cudaFree would synchronise the whole device); other streams and contexts
+    // keep running
+    cudaStream_t cs = ctx->cstream[0];
+    cudaError_t e = ctx->ring_used ? cudaEventSynchronize(ctx->ev_ring_done) : cudaSuccess;
+    if (e == cudaSuccess && hp.buf_bytes > ctx->ring_bytes) {
+        if (ctx->ring) e = cudaFreeAsync(ctx->ring, cs);
+        ctx->bytes -= 2 * ctx->ring_bytes;
+        ctx->ring = nullptr;
+        ctx->ring_bytes = 0;
+        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&ctx->ring), 2 * hp.buf_bytes, cs);
+        if (e == cudaSuccess) {
+            ctx->ring_bytes = hp.buf_bytes;
+            ctx->bytes += 2 * hp.buf_bytes;
+        }
+    }
+    if (e == cudaSuccess && hp.records > ctx->ring_out_records) {
+        if (ctx->ring_out) e = cudaFreeAsync(ctx->ring_out, cs);
+        ctx->bytes -= ctx->ring_out_records * sizeof(ttc_level_result);
+        ctx->ring_out = nullptr;
+        ctx->ring_out_records = 0;
+        if (e == cudaSuccess)
+            e = cudaMallocAsync(reinterpret_cast<void **>(&ctx->ring_out), hp.records * sizeof(ttc_level_result), cs);
+        if (e == cudaSuccess) {
+            ctx->ring_out_records = hp.records;
+            ctx->bytes += hp.records * sizeof(ttc_level_result);
+        }
+    }
+    // the new buffers are usable from any stream once the copy stream has made them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    return FT_OK;
+}
+
+extern "C" ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
+                                             int dtype, int H, int W, int64_t pitch_bytes, int levels, int mode,
+                                             ttc_level_result *out, void *stream)
+{
+    if (!ctx || !frames || !out) return FT_ERR_INVALID_ARG;
+    if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
+    if (!ctx->ring_ready) return FT_ERR_CUDA;
+    HostPlan hp;
+    ft_status st = host_plan(ctx, frame_stride_bytes, T, dtype, H, W, pitch_bytes, levels, &hp);
+    if (st != FT_OK) return st;
+    // the ring is sized by ttc_ctx_reserve_host: nothing is allocated here
+    if (hp.buf_bytes > ctx->ring_bytes || hp.records > ctx->ring_out_records) return FT_ERR_WORKSPACE;
+    const int npairs = T - 1;
+    const int lead = hp.lead, chunk = hp.chunk, nchunks = hp.nchunks;
+    const size_t frame_bytes = hp.frame_bytes;
     cudaStream_t s = ft::as_stream(stream);
     const unsigned char *host = static_cast<const unsigned char *>(frames);
     cudaError_t e = cudaEventRecord(ctx->ev_start, s);
@@ -1248,6 +1291,8 @@ extern "C" ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, i
         // the buffer is free once the chunk two back has been computed (or, for the
         // first two chunks, once the stream has reached this call)
         e = cudaStreamWaitEvent(cs, k < 2 ? ctx->ev_start : ctx->ev_free[b], 0);
+        // and, on any stream, once the previous call has finished with the ring
+        if (e == cudaSuccess && k < 2 && ctx->ring_used) e = cudaStreamWaitEvent(cs, ctx->ev_ring_done, 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(dev, host + (size_t)f0 * frame_stride_bytes,
                                 (size_t)(n + x) * frame_stride_bytes + frame_bytes, cudaMemcpyHostToDevice, cs);
@@ -1266,6 +1311,8 @@ extern "C" ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, i
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, ctx->ring_out, (size_t)npairs * levels * sizeof(ttc_level_result),
                             cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_ring_done, s);
+    if (e == cudaSuccess) ctx->ring_used = true;
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
         return FT_ERR_CUDA;

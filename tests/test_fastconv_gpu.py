@@ -305,25 +305,53 @@ def test_fastconv_fft_errors_and_auto_switch():
     import ctypes
     dims = (ctypes.c_int64 * 4)(2, 2, 8, 8)
     kd = (ctypes.c_int64 * 4)(1, 1, 3, 3)
+    h = ctypes.c_void_p()
     b = ctypes.c_size_t()
-    assert L.fastconv_fft_workspace(dims, 4, kd, ctypes.byref(b)) == 3          # rank 4
+    assert L.fastconv_fft_plan_create(dims, 4, kd, ctypes.byref(h), ctypes.byref(b)) == 3      # rank 4
+    assert not h.value
     dev = torch.device("cuda")
     x = torch.rand((64, 64), device=dev)
     k = torch.rand((5, 5), device=dev)
     with pytest.raises(ft.FtError):
         _fft_small_workspace(L, x, k)                                    # workspace too small
     small = ft.fastconv(x, k)                                   # below the threshold: direct
-    big = ft.fastconv(x, torch.rand((41, 41), device=dev))      # at or above: FFT
+    big = ft.fastconv(x, torch.rand((41, 41), device=dev))      # small image: direct as well
     assert small.shape == (68, 68) and big.shape == (104, 104)
-    assert L.fastconv_prefers_fft((ctypes.c_int64 * 2)(64, 64), 2, (ctypes.c_int64 * 2)(29, 29)) == 0
-    assert L.fastconv_prefers_fft((ctypes.c_int64 * 2)(64, 64), 2, (ctypes.c_int64 * 2)(31, 31)) == 1
+    d2, d3 = (ctypes.c_int64 * 2), (ctypes.c_int64 * 3)
+    assert L.fastconv_prefers_fft(d2(1080, 1920), 2, d2(29, 29)) == 0
+    assert L.fastconv_prefers_fft(d2(1080, 1920), 2, d2(31, 31)) == 1
+    assert L.fastconv_prefers_fft(d2(64, 64), 2, d2(31, 31)) == 0                # output area too small
+    assert L.fastconv_prefers_fft(d3(64, 256, 256), 3, d3(10, 10, 10)) == 0      # 3-D: not measured
+
+
+def test_fastconv_fft_two_streams_one_plan_bitwise():
+    """One plan, two streams with their own workspaces, calls interleaved: each output
+    bitwise equal to the same call made alone on the default stream."""
+    dev = torch.device("cuda")
+    E = [torch.from_numpy(scenes.uniform_array((300, 400), seed=s)).to(dev) for s in (1, 2)]
+    k = torch.from_numpy(scenes.normal_array((33, 33), seed=3)).to(dev)
+    plan = ft.FftPlan((300, 400), (33, 33), dev)
+    ref = [plan(e, k).clone() for e in E]
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ws = [plan.new_workspace(), plan.new_workspace()]
+    outs = [torch.empty_like(ref[0]), torch.empty_like(ref[1])]
+    for _ in range(5):
+        for i in (0, 1):
+            streams[i].wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(streams[i]):
+                plan(E[i], k, out=outs[i], workspace=ws[i])
+    torch.cuda.synchronize()
+    for i in (0, 1):
+        assert torch.equal(outs[i], ref[i])
+    plan.close()
 
 
 def _fft_small_workspace(L, x, k):
-    import ctypes
+    plan = ft.FftPlan(tuple(x.shape), tuple(k.shape), x.device)
     out = torch.empty((68, 68), device=x.device)
-    ws = torch.empty(16, dtype=torch.uint8, device=x.device)
-    st = L.fastconv_fft(x.data_ptr(), (ctypes.c_int64 * 2)(64, 64), 2, k.data_ptr(), (ctypes.c_int64 * 2)(5, 5),
-                        out.data_ptr(), ws.data_ptr(), 16, None)
+    ws = torch.empty(256, dtype=torch.uint8, device=x.device)
+    st = L.fastconv_fft(plan._h, x.data_ptr(), k.data_ptr(), out.data_ptr(), ws.data_ptr(), 256, None)
+    plan.close()
     if st != 0:
         raise ft.FtError(st, "fastconv_fft")

@@ -364,3 +364,45 @@ def test_gradient_errors():
     assert L.ttc_gradient(x.data_ptr(), 0, 1, 4, 4, out.data_ptr(), None, None) == 2
     assert L.ttc_gradient(x.data_ptr(), 0, 4, 4, 3, out.data_ptr(), None, None) == 2
     assert L.ttc_gradient(x.data_ptr(), 7, 4, 4, 4, out.data_ptr(), None, None) == 1
+
+
+def test_reserve_host_waits_only_for_its_own_context():
+    """Growing one context's host-sequence buffers does not synchronise the device: a
+    long kernel on another stream is still running when the reservation returns; both
+    contexts then give bitwise the same records for the same host video."""
+    H, W, levels = 96, 160, 3
+    sc = scenes.tilted_plane_scene(H=H, W=W, seed=31, m=16)
+    frames = scenes.render_sequence(sc, 24).pin_memory()
+    a = ft.TtcContext(H, W, levels, 23)
+    b = ft.TtcContext(H, W, levels, 23)
+    b.reserve_host(frames[:4], levels=levels)              # small buffers first
+    other = torch.cuda.Stream()
+    with torch.cuda.stream(other):
+        torch.cuda._sleep(int(2e9))                        # about a second of GPU clock
+    b.reserve_host(frames, levels=levels)                  # grows: frees and allocates
+    assert not other.query(), "the reservation waited for another stream's work"
+    ra = ft.results_to_numpy(a.solve_sequence(frames, levels=levels, mode=1))
+    rb = ft.results_to_numpy(b.solve_sequence(frames, levels=levels, mode=1))
+    torch.cuda.synchronize()
+    assert ra.tobytes() == rb.tobytes()
+    dev = ft.results_to_numpy(a.solve_sequence(frames.to(DEV), levels=levels, mode=1))
+    assert dev.tobytes() == ra.tobytes()
+    a.close()
+    b.close()
+
+
+def test_host_sequence_needs_reserved_buffers():
+    L = ft.load()
+    H, W = 64, 96
+    fr = torch.zeros((5, H, W), dtype=torch.uint8).pin_memory()
+    ctx = ft.TtcContext(H, W, 2, 4)
+    out = torch.empty(4 * 2 * ft.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    st = L.ttc_solve_sequence_host(ctx._h, fr.data_ptr(), H * W, 5, 0, H, W, W, 2, 1, out.data_ptr(),
+                                   torch.cuda.current_stream().cuda_stream)
+    assert st == 4                                          # FT_ERR_WORKSPACE: nothing reserved
+    ctx.reserve_host(fr, levels=2)
+    st = L.ttc_solve_sequence_host(ctx._h, fr.data_ptr(), H * W, 5, 0, H, W, W, 2, 1, out.data_ptr(),
+                                   torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    torch.cuda.synchronize()
+    ctx.close()
