@@ -210,6 +210,14 @@ def _stream_ptr(t: torch.Tensor) -> int:
     return torch.cuda.current_stream(t.device).cuda_stream
 
 
+def _cuda_device(device=None) -> torch.device:
+    """A CUDA device with its index (the current device when none is given)."""
+    d = torch.device(device) if device is not None else torch.device("cuda")
+    if d.type != "cuda":
+        raise ValueError("a CUDA device is needed")
+    return d if d.index is not None else torch.device("cuda", torch.cuda.current_device())
+
+
 def _require_cuda(t: torch.Tensor, name: str):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
@@ -280,7 +288,7 @@ class FftPlan:
 
     def __init__(self, shape, kshape, device=None):
         L = load()
-        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = _cuda_device(device)
         self.shape, self.kshape = tuple(int(v) for v in shape), tuple(int(v) for v in kshape)
         if len(self.shape) != len(self.kshape):
             raise ValueError("shape and kshape must have the same rank")

@@ -16,6 +16,8 @@
 
 #include "common.cuh"
 #include "ttc_pass.cuh"
+#include "ttc_levels.cuh"
+#include "ttc_merge.cuh"
 #include "ttc_tma.cuh"
 
 #include <cudaTypedefs.h>
@@ -23,6 +25,8 @@
 namespace {
 
 using ttc_pass::NSUM;
+using ttc_merge::SolveDesc;
+using ttc_merge::merge_solve;
 using ttc_pass::TR;
 using ttc_pass::TC;
 
@@ -42,102 +46,6 @@ struct SolveParams {
     int skip;                         // pairs [0, skip) are not written
 };
 
-__device__ void solve_one(const double s[NSUM], int mode, int level, ttc_level_result *r)
-{
-    double th[3] = {0.0, 0.0, 0.0};
-    int flags = 0;
-    if (mode == FT_MODE_TTC) {
-        if (!(s[5] > 0.0)) flags |= FT_FLAG_SINGULAR;
-        else th[2] = -s[8] / s[5];
-    } else {
-        // M [A B C]^T = -[s6 s7 s8]^T with M = [[s0 s1 s3] [s1 s2 s4] [s3 s4 s5]],
-        // scaled to unit diagonal, inverted by its adjugate (Sec. V-A).
-        const double m[3][3] = {{s[0], s[1], s[3]}, {s[1], s[2], s[4]}, {s[3], s[4], s[5]}};
-        double dsc[3];
-        for (int i = 0; i < 3; ++i) {
-            if (!(m[i][i] > 0.0)) flags |= FT_FLAG_SINGULAR;
-            dsc[i] = m[i][i] > 0.0 ? rsqrt(m[i][i]) : 0.0;
-        }
-        if (!flags) {
-            double u[3][3];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) u[i][j] = dsc[i] * m[i][j] * dsc[j];
-            const double rhs[3] = {-s[6] * dsc[0], -s[7] * dsc[1], -s[8] * dsc[2]};
-            const double c00 = u[1][1] * u[2][2] - u[1][2] * u[2][1];
-            const double c01 = u[0][2] * u[2][1] - u[0][1] * u[2][2];
-            const double c02 = u[0][1] * u[1][2] - u[0][2] * u[1][1];
-            const double c10 = u[1][2] * u[2][0] - u[1][0] * u[2][2];
-            const double c11 = u[0][0] * u[2][2] - u[0][2] * u[2][0];
-            const double c12 = u[0][2] * u[1][0] - u[0][0] * u[1][2];
-            const double c20 = u[1][0] * u[2][1] - u[1][1] * u[2][0];
-            const double c21 = u[0][1] * u[2][0] - u[0][0] * u[2][1];
-            const double c22 = u[0][0] * u[1][1] - u[0][1] * u[1][0];
-            const double det = u[0][0] * c00 + u[0][1] * c10 + u[0][2] * c20;
-            if (!(det > 1e-12)) {
-                flags |= FT_FLAG_SINGULAR;
-            } else {
-                th[0] = dsc[0] * ((c00 * rhs[0] + c01 * rhs[1] + c02 * rhs[2]) / det);
-                th[1] = dsc[1] * ((c10 * rhs[0] + c11 * rhs[1] + c12 * rhs[2]) / det);
-                th[2] = dsc[2] * ((c20 * rhs[0] + c21 * rhs[1] + c22 * rhs[2]) / det);
-            }
-        }
-    }
-    r->level = level;
-    r->flags = flags;
-    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-    if (flags & FT_FLAG_SINGULAR) {
-        r->A = r->B = r->C = r->ttc = r->x0 = r->y0 = r->resid = qnan;
-        return;
-    }
-    const double A = th[0], B = th[1], C = th[2];
-    r->A = A;
-    r->B = B;
-    r->C = C;
-    const double scale = (double)(1 << level);
-    if (C == 0.0) {
-        r->flags |= FT_FLAG_C_ZERO;
-        r->ttc = __longlong_as_double(0x7ff0000000000000LL);
-        r->x0 = r->y0 = qnan;
-    } else {
-        r->ttc = 1.0 / C;
-        r->x0 = -A / C * scale;
-        r->y0 = -B / C * scale;
-        if (C < 0.0) r->flags |= FT_FLAG_RECEDING;
-    }
-    // sum (A Ex + B Ey + C G + Et)^2 = th' M th + 2 th' [s6 s7 s8] + s9
-    const double m0 = s[0] * A + s[1] * B + s[3] * C;
-    const double m1 = s[1] * A + s[2] * B + s[4] * C;
-    const double m2 = s[3] * A + s[4] * B + s[5] * C;
-    const double res = (A * m0 + B * m1 + C * m2) + 2.0 * (A * s[6] + B * s[7] + C * s[8]) + s[9];
-    r->resid = s[9] > 0.0 ? res / s[9] : 0.0;
-}
-
-// One warp: FP64 merge of ntiles FP32 tile partials in a fixed order (lane-strided,
-// then a shuffle tree), scaling to level-l mean-image units, solve; lane 0 writes.
-__device__ __forceinline__ void merge_solve(const float *src, int ntiles, int l, double inv_scale, int64_t ncubes,
-                                            int mode, const int *status, ttc_level_result *out)
-{
-    const int lane = threadIdx.x;
-    double acc[NSUM];
-#pragma unroll
-    for (int s = 0; s < NSUM; ++s) acc[s] = 0.0;
-    for (int t = lane; t < ntiles; t += 32)
-#pragma unroll
-        for (int s = 0; s < NSUM; ++s) acc[s] += (double)src[t * NSUM + s];
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1)
-#pragma unroll
-        for (int s = 0; s < NSUM; ++s) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
-    if (lane == 0) {
-        ttc_level_result r;
-        for (int s = 0; s < NSUM; ++s) r.sums[s] = acc[s] * inv_scale;
-        r.n = ncubes;
-        solve_one(r.sums, mode, l, &r);
-        if (*status) r.flags |= FT_FLAG_TIMEOUT;
-        *out = r;
-    }
-}
-
 __global__ void __launch_bounds__(32)
 ttc_solve_kernel(const SolveParams p)
 {
@@ -149,19 +57,12 @@ ttc_solve_kernel(const SolveParams p)
                 p.mode, p.status, p.out + item);
 }
 
-// partials and cube count of one (pair, level) of a batch
-struct SolveDesc {
-    int64_t poff;                     // floats into the partials
-    int64_t ncubes;
-    int ntiles, level;
-};
-
 __global__ void __launch_bounds__(32)
 ttc_batch_solve_kernel(const float *partials, const SolveDesc *sd, int mode, const int *status,
                        ttc_level_result *out)
 {
     const SolveDesc d = sd[blockIdx.x];          // blockIdx.x = pair * levels + level
-    merge_solve(partials + d.poff, d.ntiles, d.level, ldexp(1.0, -4 - 4 * d.level), d.ncubes, mode, status,
+    merge_solve(partials + d.poff, d.ntiles, d.level, ldexp(1.0, -4 - 4 * d.level - d.shift), d.ncubes, mode, status,
                 out + blockIdx.x);
 }
 
@@ -338,6 +239,7 @@ struct Geometry {
     int64_t pitch[FT_MAX_LEVELS];     // bytes
     int64_t fstride[FT_MAX_LEVELS];   // bytes between frames
     int64_t ioff[FT_MAX_LEVELS];      // bytes, start of level l images
+    int shift[FT_MAX_LEVELS];         // the level's partials are 2^shift times the block-sum sums
     int64_t partial_floats, image_bytes;
 };
 
@@ -361,6 +263,7 @@ void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geom
         else if ((int64_t)(plan_pairs ? plan_pairs : npairs) * ft::ceil_div(g.H[l] - 1, TR) * g.tiles_x[l] < 1216)
             tr = ttc_pass::TR_SMALL;
         g.tr[l] = tr;
+        g.shift[l] = 0;
         g.tiles_y[l] = (int)ft::ceil_div(g.H[l] - 1, tr);
         g.ntiles[l] = g.tiles_y[l] * g.tiles_x[l];
         g.poff[l] = po;
@@ -391,6 +294,7 @@ struct ttc_ctx {
     float *partials;
     unsigned char *images;
     int *status;              // stage-1 timeout flag
+    int *counters;            // 64 bytes after status: the levels kernel's ticket [0] and tile counts [32...]
     int64_t partial_cap;      // floats
     int64_t image_cap;        // bytes
     size_t bytes;
@@ -402,7 +306,13 @@ struct ttc_ctx {
     ttc_pass::PassParams *d_descs;    // [max_levels][max_pairs]
     int *d_prefix;                    // [max_levels][2][max_pairs + 1]
     SolveDesc *d_sdesc;               // [max_pairs * max_levels]
-    unsigned char *h_stage;           // pinned staging buffer of the three arrays
+    CUtensorMap *d_maps;              // [max_pairs][4]: level-0 maps of pairs the TMA kernel takes
+    int2 *d_items;                    // [items_cap]: (pair, tile) of the TMA kernel's level-0 items
+    size_t items_cap;
+    int2 *d_items1;                   // [items1_cap]: (pair, tile) of the levels kernel's items
+    size_t items1_cap;
+    size_t off_maps, off_items, off_items1;   // byte offsets of those arrays in the staging buffers
+    unsigned char *h_stage;           // pinned staging buffer of the arrays
     size_t stage_bytes;
     cudaEvent_t stage_ev;             // the last upload from h_stage
     bool stage_pending;
@@ -410,6 +320,9 @@ struct ttc_ctx {
         int npairs, levels, dtype;
         int rpw[FT_MAX_LEVELS], in_es[FT_MAX_LEVELS], out_es[FT_MAX_LEVELS];
         int n_int[FT_MAX_LEVELS], n_edge[FT_MAX_LEVELS];
+        int n_tma;                    // level-0 items of the TMA kernel (uint8 pairs it can read)
+        int lbegin[FT_MAX_LEVELS + 1];  // levels kernel: first item of level l (l >= 1)
+        bool fused;                   // levels >= 1 and the solve run in the levels kernel
         bool ready;
     } b;
     int plan_rpw[FT_MAX_LEVELS];      // tile rows per warp per level for batches (0: automatic)
@@ -446,8 +359,9 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     const int64_t ib = std::max(g.image_bytes, g16.image_bytes);
     float *part = nullptr;
     unsigned char *img = nullptr;
-    // the partials, then 256 bytes holding the status word
-    cudaError_t e = cudaMalloc(&part, (size_t)pf * sizeof(float) + 256);
+    // the partials, then the status word and (64 bytes on) the levels kernel's counters
+    const size_t cbytes = ((64 + (32 + (size_t)max_levels * max_pairs) * sizeof(int)) + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&part, (size_t)pf * sizeof(float) + cbytes);
     if (e == cudaSuccess && ib > 0) e = cudaMalloc(&img, (size_t)ib);
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
@@ -467,16 +381,28 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->partials = part;
     c->images = img;
     c->status = reinterpret_cast<int *>(part + pf);
+    c->counters = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(c->status) + 64);
     c->partial_cap = pf;
     c->image_cap = ib;
-    c->bytes = (size_t)pf * sizeof(float) + 256 + (size_t)ib;
+    c->bytes = (size_t)pf * sizeof(float) + cbytes + (size_t)ib;
     c->ready = false;
     // batch descriptors
     const size_t nd = (size_t)max_levels * max_pairs;
     const size_t b_desc = nd * sizeof(ttc_pass::PassParams);
     const size_t b_pre = (size_t)max_levels * 2 * (max_pairs + 1) * sizeof(int);
     const size_t b_sd = nd * sizeof(SolveDesc);
-    c->stage_bytes = b_desc + b_pre + b_sd;
+    // level-0 tensor maps (64-byte aligned) and the TMA kernel's item table
+    const size_t tiles0 = (size_t)ft::ceil_div(max_H - 1, TR) * (size_t)ft::ceil_div(max_W - 1, TC);
+    c->items_cap = tiles0 * (size_t)max_pairs;
+    c->off_maps = (b_desc + b_pre + b_sd + 127) / 128 * 128;
+    c->off_items = c->off_maps + (size_t)max_pairs * 4 * sizeof(CUtensorMap);
+    // levels >= 1 of every pair, at the smaller tile height (the most tiles)
+    size_t tiles1 = 0;
+    for (int l = 1; l < max_levels && (max_H >> l) >= 2 && (max_W >> l) >= 2; ++l)
+        tiles1 += (size_t)ft::ceil_div((max_H >> l) - 1, ttc_pass::TR_SMALL) * (size_t)ft::ceil_div((max_W >> l) - 1, TC);
+    c->items1_cap = tiles1 * (size_t)max_pairs;
+    c->off_items1 = c->off_items + c->items_cap * sizeof(int2);
+    c->stage_bytes = c->off_items1 + c->items1_cap * sizeof(int2);
     unsigned char *dbuf = nullptr;
     e = cudaMalloc(&dbuf, c->stage_bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(&c->h_stage, c->stage_bytes, cudaHostAllocDefault);
@@ -506,6 +432,9 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->d_descs = reinterpret_cast<ttc_pass::PassParams *>(dbuf);
     c->d_prefix = reinterpret_cast<int *>(dbuf + b_desc);
     c->d_sdesc = reinterpret_cast<SolveDesc *>(dbuf + b_desc + b_pre);
+    c->d_maps = reinterpret_cast<CUtensorMap *>(dbuf + c->off_maps);
+    c->d_items = reinterpret_cast<int2 *>(dbuf + c->off_items);
+    c->d_items1 = reinterpret_cast<int2 *>(dbuf + c->off_items1);
     c->bytes += c->stage_bytes;
     *ctx = c;
     if (!c->ring_ready) {
@@ -572,6 +501,39 @@ bool u8_frame_map(CUtensorMap *m, const void *base, int W, int H, int npairs, in
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// the persistent TMA level-0 kernel over a set of work items: two CTAs per SM
+template <class Items, bool GLOBAL_MAPS>
+cudaError_t launch_tma_items_w(const Items &it, bool write, int *status, cudaStream_t s)
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(it.total, 2 * std::max(nsm, 1));
+    if (grid <= 0) return cudaSuccess;
+    const unsigned extra = ft::tma_extra_tx();
+    cudaError_t e;
+    if (write) {
+        auto k = ttc_tma::ttc_pass_tma_kernel<true, Items, GLOBAL_MAPS>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, ttc_tma::SMEM);
+        if (e == cudaSuccess) k<<<grid, ttc_pass::NT, ttc_tma::SMEM, s>>>(it, status, extra);
+    } else {
+        auto k = ttc_tma::ttc_pass_tma_kernel<false, Items, GLOBAL_MAPS>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, ttc_tma::SMEM);
+        if (e == cudaSuccess) k<<<grid, ttc_pass::NT, ttc_tma::SMEM, s>>>(it, status, extra);
+    }
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+cudaError_t launch_tma_items(const ttc_tma::VideoItems &it, bool write, int *status, cudaStream_t s)
+{
+    return launch_tma_items_w<ttc_tma::VideoItems, false>(it, write, status, s);
+}
+
+cudaError_t launch_tma_items(const ttc_tma::BatchItems &it, bool write, int *status, cudaStream_t s)
+{
+    return launch_tma_items_w<ttc_tma::BatchItems, true>(it, write, status, s);
+}
+
 // level 0 of uint8 frames by the persistent TMA kernel; false when the frames do not
 // meet the copy engine's alignment rules (the caller then uses the load path)
 bool launch_level0_tma(const ttc_pass::PassParams &p, const void *prev, const void *cur, int64_t pair_stride,
@@ -584,33 +546,15 @@ bool launch_level0_tma(const ttc_pass::PassParams &p, const void *prev, const vo
     int64_t ps = pair_stride;
     if (npairs == 1) ps = (pitch * p.H + 15) / 16 * 16;
     else if (ps <= 0 || (ps & 15)) return false;
-    CUtensorMap ma, mb, xa, xb;
-    if (!u8_frame_map(&ma, prev, p.W, p.H, npairs, pitch, ps, ttc_tma::BW) ||
-        !u8_frame_map(&mb, cur, p.W, p.H, npairs, pitch, ps, ttc_tma::BW) ||
-        !u8_frame_map(&xa, prev, p.W, p.H, npairs, pitch, ps, ttc_tma::XW) ||
-        !u8_frame_map(&xb, cur, p.W, p.H, npairs, pitch, ps, ttc_tma::XW))
+    ttc_tma::VideoItems it{};
+    if (!u8_frame_map(&it.m[0], prev, p.W, p.H, npairs, pitch, ps, ttc_tma::BW) ||
+        !u8_frame_map(&it.m[1], cur, p.W, p.H, npairs, pitch, ps, ttc_tma::BW) ||
+        !u8_frame_map(&it.m[2], prev, p.W, p.H, npairs, pitch, ps, ttc_tma::XW) ||
+        !u8_frame_map(&it.m[3], cur, p.W, p.H, npairs, pitch, ps, ttc_tma::XW))
         return false;
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    ttc_tma::TmaParams tp{};
-    tp.p = p;
-    tp.total = npairs * p.ntiles;
-    tp.status = status;
-    tp.extra_tx = ft::tma_extra_tx();
-    const int grid = std::min(tp.total, 2 * std::max(nsm, 1));
-    if (p.next) {
-        *err = cudaFuncSetAttribute(ttc_tma::ttc_pass_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    ttc_tma::SMEM);
-        if (*err == cudaSuccess)
-            ttc_tma::ttc_pass_tma_kernel<true><<<grid, ttc_pass::NT, ttc_tma::SMEM, s>>>(ma, mb, xa, xb, tp);
-    } else {
-        *err = cudaFuncSetAttribute(ttc_tma::ttc_pass_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    ttc_tma::SMEM);
-        if (*err == cudaSuccess)
-            ttc_tma::ttc_pass_tma_kernel<false><<<grid, ttc_pass::NT, ttc_tma::SMEM, s>>>(ma, mb, xa, xb, tp);
-    }
-    if (*err == cudaSuccess) *err = cudaGetLastError();
+    it.p = p;
+    it.total = npairs * p.ntiles;
+    *err = launch_tma_items(it, p.next != nullptr, status, s);
     return true;
 }
 
@@ -623,10 +567,53 @@ cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs
 
 // all levels of npairs pairs: pair p is (prev + p * pair_stride, cur + p * pair_stride);
 // independent = 0 for the consecutive pairs of a video (frame t+1 shared)
+// the levels kernel takes levels 1 .. L-1 in one launch when their images have one pixel
+// type: uint16 (uint8 frames, at most 5 levels) or float (float frames)
+bool levels_kernel_fits(int dtype, int levels)
+{
+    return levels >= 2 && (dtype == FT_F32 || levels <= 5);
+}
+
+// merge + solve requested from launch_partials (fused into the levels kernel)
+struct SolveReq {
+    int mode;
+    ttc_level_result *out;
+    int skip;                         // pairs [0, skip) are not written
+};
+
+int sm_count()
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(nsm, 1);
+}
+
+template <typename Tin, bool VIDEO>
+cudaError_t launch_levels_t(const ttc_levels::LevelsParams &lp, cudaStream_t s)
+{
+    const int total = lp.begin[lp.levels];
+    if (total <= 0) return cudaSuccess;
+    const int grid = std::min(total, FT_TTC_MINB * sm_count());
+    ttc_levels::ttc_levels_kernel<Tin, VIDEO><<<grid, ttc_pass::NT, 0, s>>>(lp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_levels(const ttc_levels::LevelsParams &lp, int dtype, bool video, cudaStream_t s)
+{
+    if (dtype == FT_U8)
+        return video ? launch_levels_t<unsigned short, true>(lp, s) : launch_levels_t<unsigned short, false>(lp, s);
+    return video ? launch_levels_t<float, true>(lp, s) : launch_levels_t<float, false>(lp, s);
+}
+
+// all levels of npairs pairs: pair p is (prev + p * pair_stride, cur + p * pair_stride);
+// independent = 0 for the consecutive pairs of a video (frame t+1 shared).  With `req`,
+// the merge + solve runs inside the levels kernel when that kernel is used (*solved).
 ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64_t pair_stride, int npairs,
                           int independent, int dtype, int H, int W, int64_t pitch, int levels, cudaStream_t s,
-                          int plan_pairs = 0)
+                          int plan_pairs = 0, const SolveReq *req = nullptr, bool *solved = nullptr)
 {
+    if (solved) *solved = false;
     if (!ctx || !prev || !cur) return FT_ERR_INVALID_ARG;
     if (npairs < 1) return FT_ERR_SHAPE;
     ft_status st = check_frames(dtype, H, W, pitch);
@@ -644,8 +631,11 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
     const uintptr_t al = dtype == FT_U8 ? 3 : 15;
     const int vec0 = ((reinterpret_cast<uintptr_t>(prev) & al) == 0 && (reinterpret_cast<uintptr_t>(cur) & al) == 0 &&
                       (pitch & (int64_t)al) == 0 && (pair_stride & (int64_t)al) == 0) ? 1 : 0;
+    ttc_pass::PassParams pp[FT_MAX_LEVELS];
+    int out_es[FT_MAX_LEVELS];
     for (int l = 0; l < levels; ++l) {
-        ttc_pass::PassParams p{};
+        ttc_pass::PassParams &p = pp[l];
+        p = ttc_pass::PassParams{};
         if (l == 0) {
             p.prev = static_cast<const unsigned char *>(prev);
             p.cur = static_cast<const unsigned char *>(cur);
@@ -669,38 +659,82 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
         p.xoff = (float)(0.5 - ((double)W - pl) / (2.0 * pl));
         p.yoff = (float)(0.5 - ((double)H - pl) / (2.0 * pl));
         p.partials = ctx->partials + g.poff[l];
-        int out_es = 4;
+        out_es[l] = 4;
         if (l + 1 < levels) {
             p.next = ctx->images + g.ioff[l + 1];
             p.next_fstride = g.fstride[l + 1];
             p.next_pitch = g.pitch[l + 1];
-            out_es = g.esize[l + 1];
+            out_es[l] = g.esize[l + 1];
         }
         p.write_prev = independent;
-        const int in_es = g.esize[l];
-        cudaError_t e = cudaSuccess;
-        if (l == 0) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
-        if (e == cudaSuccess && l == 0 && ctx->ev0_start) e = cudaEventRecord(ctx->ev0_start, s);
-        if (e != cudaSuccess) {
-            ft::set_cuda_error(e);
-            return FT_ERR_CUDA;
-        }
         p.vec = l == 0 ? vec0 : 1;
         p.padded = l == 0 ? 0 : 1;
+    }
+    const bool fused = levels_kernel_fits(dtype, levels);
+    // the status word and, after it, the levels kernel's ticket and tile counters
+    const size_t zero_bytes = fused ? 64 + (32 + (size_t)levels * npairs) * sizeof(int) : sizeof(int);
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, zero_bytes, s);
+    if (e == cudaSuccess && ctx->ev0_start) e = cudaEventRecord(ctx->ev0_start, s);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
+    }
+    for (int l = 0; l < (fused ? 1 : levels); ++l) {
+        const ttc_pass::PassParams &p = pp[l];
+        const int in_es = g.esize[l];
         bool done = false;
-        if (l == 0 && dtype == FT_U8 && g.tr[0] == TR && (out_es == 2 || !p.next)) {
+        if (l == 0 && dtype == FT_U8 && g.tr[0] == TR && (out_es[0] == 2 || !p.next)) {
             done = launch_level0_tma(p, prev, cur, pair_stride, npairs, ctx->status, s, &e);
-            if (done) ++launches;
+            if (done) {
+                ++launches;
+                g.shift[0] = 16;            // pixels scaled by 256 in the TMA pass
+            }
         }
         if (done) {
-        } else if (in_es == 1) e = launch_pass<unsigned char>(p, out_es, npairs, s, &launches);
-        else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es, npairs, s, &launches);
-        else e = launch_pass<float>(p, out_es, npairs, s, &launches);
+        } else if (in_es == 1) e = launch_pass<unsigned char>(p, out_es[l], npairs, s, &launches);
+        else if (in_es == 2) e = launch_pass<unsigned short>(p, out_es[l], npairs, s, &launches);
+        else e = launch_pass<float>(p, out_es[l], npairs, s, &launches);
         if (e == cudaSuccess && l == 0 && ctx->ev0_end) e = cudaEventRecord(ctx->ev0_end, s);
         if (e != cudaSuccess) {
             ft::set_cuda_error(e);
             return FT_ERR_CUDA;
         }
+    }
+    if (fused) {
+        ttc_levels::LevelsParams lp{};
+        lp.levels = levels;
+        lp.npairs = npairs;
+        lp.begin[1] = 0;
+        for (int l = 1; l < levels; ++l) {
+            lp.lvl[l] = pp[l];
+            lp.ntiles[l] = g.ntiles[l];
+            lp.rpw[l] = g.tr[l] / 8;
+            lp.begin[l + 1] = lp.begin[l] + npairs * g.ntiles[l];
+        }
+        for (int l = 0; l < levels; ++l) lp.ntiles[l] = g.ntiles[l];
+        lp.tickets = ctx->counters;
+        lp.done = ctx->counters + 32;
+        lp.status = ctx->status;
+        if (req) {
+            lp.solve = 1;
+            lp.mode = req->mode;
+            lp.skip = req->skip;
+            lp.out = req->out;
+            lp.partials = ctx->partials;
+            for (int l = 0; l < levels; ++l) {
+                lp.poff[l] = g.poff[l];
+                lp.inv_scale[l] = std::ldexp(1.0, -4 - 4 * l - g.shift[l]);
+                lp.ncubes[l] = (int64_t)(g.H[l] - 1) * (int64_t)(g.W[l] - 1);
+            }
+        }
+        if ((int64_t)lp.begin[levels] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
+        e = launch_levels(lp, dtype, true, s);
+        if (e != cudaSuccess) {
+            ft::set_cuda_error(e);
+            return FT_ERR_CUDA;
+        }
+        ++launches;
+        if (req && solved) *solved = true;
     }
     ctx->g = g;
     ctx->ready = true;
@@ -722,7 +756,7 @@ ft_status launch_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream
     for (int l = 0; l < g.levels; ++l) {
         sp.ntiles[l] = g.ntiles[l];
         sp.poff[l] = g.poff[l];
-        sp.inv_scale[l] = std::ldexp(1.0, -4 - 4 * l);
+        sp.inv_scale[l] = std::ldexp(1.0, -4 - 4 * l - g.shift[l]);
         sp.ncubes[l] = (int64_t)(g.H[l] - 1) * (int64_t)(g.W[l] - 1);
     }
     sp.status = ctx->status;
@@ -756,9 +790,11 @@ extern "C" ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, 
 {
     if (!ctx || !prev || !cur || !out) return FT_ERR_INVALID_ARG;
     if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
+    const SolveReq req{mode, out, 0};
+    bool solved = false;
     ft_status st = launch_partials(ctx, prev, cur, 0, 1, 0, dtype, H, W, pitch_bytes, levels,
-                                   ft::as_stream(stream));
-    if (st != FT_OK) return st;
+                                   ft::as_stream(stream), 0, &req, &solved);
+    if (st != FT_OK || solved) return st;
     return launch_solve(ctx, mode, out, ft::as_stream(stream));
 }
 
@@ -808,6 +844,12 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
         }
         ctx->stage_pending = false;
     }
+    // level 0 of uint8 pairs whose frames the copy engine can address (16-byte aligned
+    // frames and pitch) runs the persistent TMA kernel when the plan has 64-row tiles
+    const bool tma_level0 = dtype == FT_U8 && rpw[0] == 8 && ft::tensor_map_encoder() != nullptr;
+    CUtensorMap *hmaps = reinterpret_cast<CUtensorMap *>(ctx->h_stage + ctx->off_maps);
+    int2 *hitems = reinterpret_cast<int2 *>(ctx->h_stage + ctx->off_items);
+    int64_t n_tma = 0;
     ttc_pass::PassParams *hd = reinterpret_cast<ttc_pass::PassParams *>(ctx->h_stage);
     int *hpre = reinterpret_cast<int *>(ctx->h_stage + nd * sizeof(ttc_pass::PassParams));
     SolveDesc *hsd = reinterpret_cast<SolveDesc *>(ctx->h_stage + nd * sizeof(ttc_pass::PassParams) +
@@ -841,6 +883,15 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
             return cur_off[l] >= 0 ? ctx->images + cur_off[l]
                                    : static_cast<unsigned char *>(d.cur_pyramid) + pyr_off[l];
         };
+        bool tma = tma_level0 && (reinterpret_cast<uintptr_t>(d.prev) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(d.cur) & 15) == 0 && (d.pitch_bytes & 15) == 0;
+        if (tma) {
+            const int64_t ps = (d.pitch_bytes * d.H + 15) / 16 * 16;
+            tma = u8_frame_map(&hmaps[4 * p + 0], d.prev, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::BW) &&
+                  u8_frame_map(&hmaps[4 * p + 1], d.cur, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::BW) &&
+                  u8_frame_map(&hmaps[4 * p + 2], d.prev, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::XW) &&
+                  u8_frame_map(&hmaps[4 * p + 3], d.cur, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::XW);
+        }
         const uintptr_t al = dtype == FT_U8 ? 3 : 15;
         const int vec0 = ((reinterpret_cast<uintptr_t>(d.prev) & al) == 0 &&
                           (reinterpret_cast<uintptr_t>(d.cur) & al) == 0 && (d.pitch_bytes & (int64_t)al) == 0)
@@ -878,8 +929,14 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
                 q.next_pitch = img_pitch[l + 1];
             }
             hd[(size_t)l * ctx->max_pairs + p] = q;
-            const int ni = q.vec ? (q.tiles_y - 1) * (q.tiles_x - 1) : 0;
-            const int ne = q.vec ? q.tiles_x + q.tiles_y - 1 : q.ntiles;
+            const bool by_tma = l == 0 && tma;
+            const int ni = by_tma ? 0 : q.vec ? (q.tiles_y - 1) * (q.tiles_x - 1) : 0;
+            const int ne = by_tma ? 0 : q.vec ? q.tiles_x + q.tiles_y - 1 : q.ntiles;
+            if (by_tma) {
+                if (n_tma + q.ntiles > (int64_t)ctx->items_cap) return FT_ERR_WORKSPACE;
+                for (int t = 0; t < q.ntiles; ++t) hitems[n_tma + t] = make_int2(p, t);
+                n_tma += q.ntiles;
+            }
             int *pi = hpre + ((size_t)l * 2 + 0) * (ctx->max_pairs + 1);
             int *pe = hpre + ((size_t)l * 2 + 1) * (ctx->max_pairs + 1);
             pi[p] = (int)n_int[l];
@@ -893,6 +950,7 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
             sd.ncubes = (int64_t)(H - 1) * (W - 1);
             sd.ntiles = q.ntiles;
             sd.level = l;
+            sd.shift = by_tma ? 16 : 0;       // the TMA kernel's pixels are scaled by 256
             hsd[(size_t)p * levels + l] = sd;
             poff += (int64_t)q.ntiles * NSUM;
             in_es[l] = l == 0 ? es0 : ((dtype == FT_U8 && l <= 4) ? 2 : 4);
@@ -902,18 +960,49 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
     if (poff > ctx->partial_cap || ioff > ctx->image_cap) return FT_ERR_WORKSPACE;
     for (int l = 0; l < levels; ++l)
         if (n_int[l] > 0x7fffffffLL || n_edge[l] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
-    cudaError_t e = cudaMemcpyAsync(ctx->d_descs, ctx->h_stage, ctx->stage_bytes, cudaMemcpyHostToDevice, s);
+    if (n_tma > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
+    // levels >= 1 in the levels kernel: items level-major, pair-major within a level
+    const bool fused = levels_kernel_fits(dtype, levels);
+    int2 *hitems1 = reinterpret_cast<int2 *>(ctx->h_stage + ctx->off_items1);
+    int64_t n1 = 0;
+    int lbegin[FT_MAX_LEVELS + 1] = {0};
+    if (fused) {
+        for (int l = 1; l < levels; ++l) {
+            lbegin[l] = (int)n1;
+            for (int p = 0; p < npairs; ++p) {
+                const int nt = hd[(size_t)l * ctx->max_pairs + p].ntiles;
+                if (n1 + nt > (int64_t)ctx->items1_cap || n1 + nt > 0x7fffffffLL) return FT_ERR_WORKSPACE;
+                for (int t = 0; t < nt; ++t) hitems1[n1 + t] = make_int2(p, t);
+                n1 += nt;
+            }
+        }
+        lbegin[levels] = (int)n1;
+    }
+    unsigned char *dstage = reinterpret_cast<unsigned char *>(ctx->d_descs);
+    cudaError_t e = cudaMemcpyAsync(dstage, ctx->h_stage, ctx->off_maps, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_tma > 0)
+        e = cudaMemcpyAsync(dstage + ctx->off_maps, ctx->h_stage + ctx->off_maps,
+                            (size_t)npairs * 4 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_tma > 0)
+        e = cudaMemcpyAsync(dstage + ctx->off_items, ctx->h_stage + ctx->off_items, (size_t)n_tma * sizeof(int2),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n1 > 0)
+        e = cudaMemcpyAsync(dstage + ctx->off_items1, ctx->h_stage + ctx->off_items1, (size_t)n1 * sizeof(int2),
+                            cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev, s);
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
         return FT_ERR_CUDA;
     }
     ctx->stage_pending = true;
+    ctx->b.fused = fused;
+    for (int l = 0; l <= levels; ++l) ctx->b.lbegin[l] = lbegin[l];
     if (pairs != ctx->h_pairs)
         for (int p = 0; p < npairs; ++p) ctx->h_pairs[p] = pairs[p];
     ctx->b.npairs = npairs;
     ctx->b.levels = levels;
     ctx->b.dtype = dtype;
+    ctx->b.n_tma = (int)n_tma;
     for (int l = 0; l < levels; ++l) {
         ctx->b.rpw[l] = rpw[l];
         ctx->b.in_es[l] = in_es[l];
@@ -940,33 +1029,61 @@ cudaError_t batch_level(ttc_ctx *ctx, int l, int *count, cudaStream_t s)
                                               count);
 }
 
-// launches of one prepared batch; level_ev (nullable): levels + 1 events around the levels
-ft_status batch_run_impl(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream_t s, cudaEvent_t *level_ev)
+// launches of one prepared batch
+ft_status batch_run_impl(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream_t s)
 {
     if (!ctx || !out) return FT_ERR_INVALID_ARG;
     if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
     if (!ctx->b.ready) return FT_ERR_INVALID_ARG;
     const auto &b = ctx->b;
     int count = 0;
-    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
-    for (int l = 0; l < b.levels && e == cudaSuccess; ++l) {
-        if (level_ev) e = cudaEventRecord(level_ev[l], s);
-        if (e != cudaSuccess) break;
+    // the status word and, after it, the levels kernel's ticket and tile counters
+    const size_t zero_bytes = b.fused ? 64 + (32 + (size_t)b.levels * b.npairs) * sizeof(int) : sizeof(int);
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, zero_bytes, s);
+    for (int l = 0; l < (b.fused ? 1 : b.levels) && e == cudaSuccess; ++l) {
+        if (l == 0 && b.n_tma > 0) {
+            ttc_tma::BatchItems it{ctx->d_descs, ctx->d_maps, ctx->d_items, b.n_tma};
+            e = launch_tma_items(it, b.levels > 1, ctx->status, s);
+            ++count;
+            if (e != cudaSuccess) break;
+        }
         if (b.in_es[l] == 1) e = batch_level<unsigned char>(ctx, l, &count, s);
         else if (b.in_es[l] == 2) e = batch_level<unsigned short>(ctx, l, &count, s);
         else e = batch_level<float>(ctx, l, &count, s);
     }
-    if (e == cudaSuccess && level_ev) e = cudaEventRecord(level_ev[b.levels], s);
-    if (e == cudaSuccess) {
-        ttc_batch_solve_kernel<<<(unsigned)(b.npairs * b.levels), 32, 0, s>>>(ctx->partials, ctx->d_sdesc, mode,
-                                                                              ctx->status, out);
-        e = cudaGetLastError();
+    if (e == cudaSuccess && b.fused) {
+        // levels 1 .. L-1 and the merge + solve of every pair in one launch
+        ttc_levels::LevelsParams lp{};
+        lp.descs = ctx->d_descs;
+        lp.desc_stride = ctx->max_pairs;
+        lp.items = ctx->d_items1;
+        lp.levels = b.levels;
+        lp.npairs = b.npairs;
+        for (int l = 0; l <= b.levels; ++l) lp.begin[l] = b.lbegin[l];
+        for (int l = 1; l < b.levels; ++l) lp.rpw[l] = b.rpw[l];
+        lp.tickets = ctx->counters;
+        lp.done = ctx->counters + 32;
+        lp.status = ctx->status;
+        lp.solve = 1;
+        lp.mode = mode;
+        lp.partials = ctx->partials;
+        lp.sdesc = ctx->d_sdesc;
+        lp.out = out;
+        if (e == cudaSuccess) e = launch_levels(lp, b.dtype, false, s);
+        ++count;
+    } else {
+        if (e == cudaSuccess) {
+            ttc_batch_solve_kernel<<<(unsigned)(b.npairs * b.levels), 32, 0, s>>>(ctx->partials, ctx->d_sdesc, mode,
+                                                                                  ctx->status, out);
+            e = cudaGetLastError();
+            ++count;
+        }
     }
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
         return FT_ERR_CUDA;
     }
-    ctx->launches = count + 1;
+    ctx->launches = count;
     return FT_OK;
 }
 
@@ -980,7 +1097,7 @@ extern "C" ft_status ttc_batch_prepare(ttc_ctx *ctx, const ttc_pair_desc *pairs,
 
 extern "C" ft_status ttc_batch_run(ttc_ctx *ctx, int mode, ttc_level_result *out, void *stream)
 {
-    return batch_run_impl(ctx, mode, out, ft::as_stream(stream), nullptr);
+    return batch_run_impl(ctx, mode, out, ft::as_stream(stream));
 }
 
 extern "C" ft_status ttc_batch_autotune(ttc_ctx *ctx, int mode, ttc_level_result *out, int reps, int *rows_per_tile,
@@ -990,36 +1107,39 @@ extern "C" ft_status ttc_batch_autotune(ttc_ctx *ctx, int mode, ttc_level_result
     if (!ctx->b.ready) return FT_ERR_INVALID_ARG;
     cudaStream_t s = ft::as_stream(stream);
     const int npairs = ctx->b.npairs, levels = ctx->b.levels, dtype = ctx->b.dtype;
-    cudaEvent_t ev[FT_MAX_LEVELS + 1];
-    int made = 0;
-    cudaError_t e = cudaSuccess;
-    for (; made <= levels && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
-    float best_ms[FT_MAX_LEVELS];
-    int best[FT_MAX_LEVELS];
-    ft_status st = FT_OK;
-    const int cand[2] = {8, 2};
-    for (int c = 0; c < 2 && st == FT_OK && e == cudaSuccess; ++c) {
-        for (int l = 0; l < levels; ++l) ctx->plan_rpw[l] = cand[c];
-        st = batch_prepare_impl(ctx, ctx->h_pairs, npairs, dtype, levels, s);
-        float ms[FT_MAX_LEVELS] = {0};
-        for (int r = 0; r <= reps && st == FT_OK; ++r) {       // the first run warms up
-            st = batch_run_impl(ctx, mode, out, s, ev);
-            if (st != FT_OK) break;
-            e = cudaEventSynchronize(ev[levels]);
-            if (e != cudaSuccess) break;
-            for (int l = 0; l < levels && r > 0; ++l) {
-                float t = 0.f;
-                cudaEventElapsedTime(&t, ev[l], ev[l + 1]);
-                ms[l] += t;
-            }
-        }
-        for (int l = 0; l < levels; ++l)
-            if (c == 0 || ms[l] < best_ms[l]) {
-                best_ms[l] = ms[l];
-                best[l] = cand[c];
-            }
+    // candidate plans (cube rows per warp per level: 8 -> 64-row tiles, 2 -> 16-row
+    // tiles): 64-row tiles down to level k and 16-row tiles below, for k = levels .. 0.
+    // 64-row tiles at level 0 let uint8 batches use the copy-engine kernel; small levels
+    // may run more, shorter CTAs.  Each plan is timed on the whole prepared batch.
+    cudaEvent_t ev[2];
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        return FT_ERR_CUDA;
     }
-    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    float best_ms = 0.f;
+    int best_k = -1;
+    ft_status st = FT_OK;
+    for (int k = levels; k >= 0 && st == FT_OK && e == cudaSuccess; --k) {
+        for (int l = 0; l < levels; ++l) ctx->plan_rpw[l] = l < k ? 8 : 2;
+        st = batch_prepare_impl(ctx, ctx->h_pairs, npairs, dtype, levels, s);
+        float ms = 0.f;
+        for (int r = 0; r <= reps && st == FT_OK; ++r) {       // the first run warms up
+            if (r == 1) e = cudaEventRecord(ev[0], s);
+            if (e == cudaSuccess) st = batch_run_impl(ctx, mode, out, s);
+        }
+        if (st != FT_OK) break;
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e == cudaSuccess && (best_k < 0 || ms < best_ms)) {
+            best_ms = ms;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
         st = FT_ERR_CUDA;
@@ -1029,8 +1149,8 @@ extern "C" ft_status ttc_batch_autotune(ttc_ctx *ctx, int mode, ttc_level_result
         return st;
     }
     for (int l = 0; l < levels; ++l) {
-        ctx->plan_rpw[l] = best[l];
-        if (rows_per_tile) rows_per_tile[l] = 8 * best[l];
+        ctx->plan_rpw[l] = l < best_k ? 8 : 2;
+        if (rows_per_tile) rows_per_tile[l] = 8 * ctx->plan_rpw[l];
     }
     return batch_prepare_impl(ctx, ctx->h_pairs, npairs, dtype, levels, s);
 }
@@ -1146,7 +1266,8 @@ extern "C" ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dt
     if ((st = check_levels(H, W, levels)) != FT_OK) return st;
     Geometry g;
     geometry(H, W, levels, dtype, 1, 2, g);
-    // layout: 256 bytes for the status word, the partials, the level images
+    // layout: 256 bytes for the status word and the levels kernel's counters, the
+    // partials, the level images
     const int64_t pbytes = 256 + (g.partial_floats * (int64_t)sizeof(float) + 255) / 256 * 256;
     if (pbytes + g.image_bytes > (int64_t)FT_NOALLOC_SCRATCH_BYTES) return FT_ERR_WORKSPACE;
     unsigned char *base = nullptr;
@@ -1158,14 +1279,18 @@ extern "C" ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dt
     c.max_levels = levels;
     c.max_pairs = 1;
     c.status = reinterpret_cast<int *>(base);
+    c.counters = reinterpret_cast<int *>(base + 64);    // ticket, then (32 ints on) one count per level
     c.partials = reinterpret_cast<float *>(base + 256);
     c.images = base + pbytes;
     c.partial_cap = g.partial_floats;
     c.image_cap = g.image_bytes;
     c.bytes = FT_NOALLOC_SCRATCH_BYTES;
     c.ready = false;
-    st = launch_partials(&c, prev, cur, 0, 1, 0, dtype, H, W, pitch_bytes, levels, ft::as_stream(stream));
-    if (st != FT_OK) return st;
+    const SolveReq req{mode, out, 0};
+    bool solved = false;
+    st = launch_partials(&c, prev, cur, 0, 1, 0, dtype, H, W, pitch_bytes, levels, ft::as_stream(stream), 0, &req,
+                         &solved);
+    if (st != FT_OK || solved) return st;
     return launch_solve(&c, mode, out, ft::as_stream(stream));
 }
 
@@ -1175,8 +1300,14 @@ extern "C" ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_
 {
     if (!ctx || !frames || !out) return FT_ERR_INVALID_ARG;
     if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
-    ft_status st = ttc_partial_sums(ctx, frames, frame_stride_bytes, T, dtype, H, W, pitch_bytes, levels, stream);
-    if (st != FT_OK) return st;
+    if (T < 2) return FT_ERR_SHAPE;
+    if (frame_stride_bytes < 0) return FT_ERR_INVALID_ARG;
+    const unsigned char *f0 = static_cast<const unsigned char *>(frames);
+    const SolveReq req{mode, out, 0};
+    bool solved = false;
+    ft_status st = launch_partials(ctx, f0, f0 + frame_stride_bytes, frame_stride_bytes, T - 1, 0, dtype, H, W,
+                                   pitch_bytes, levels, ft::as_stream(stream), 0, &req, &solved);
+    if (st != FT_OK || solved) return st;
     return launch_solve(ctx, mode, out, ft::as_stream(stream));
 }
 
@@ -1299,14 +1430,15 @@ extern "C" ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, i
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied[b], cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_copied[b], 0);
         if (e != cudaSuccess) break;
+        const SolveReq req{mode, ctx->ring_out + (size_t)f0 * levels, x};
+        bool solved = false;
         st = launch_partials(ctx, dev, dev + frame_stride_bytes, frame_stride_bytes, n + x, 0, dtype, H, W,
-                             pitch_bytes, levels, s, npairs);
+                             pitch_bytes, levels, s, npairs, &req, &solved);
         if (st != FT_OK) return st;
-        launches += ctx->launches + 1;
+        launches += ctx->launches + (solved ? 0 : 1);
         e = cudaEventRecord(ctx->ev_free[b], s);
         if (e != cudaSuccess) break;
-        st = launch_solve(ctx, mode, ctx->ring_out + (size_t)f0 * levels, s, x);
-        if (st != FT_OK) return st;
+        if (!solved && (st = launch_solve(ctx, mode, req.out, s, x)) != FT_OK) return st;
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, ctx->ring_out, (size_t)npairs * levels * sizeof(ttc_level_result),

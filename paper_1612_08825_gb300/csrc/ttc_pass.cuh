@@ -158,6 +158,21 @@ template <> struct Pix<float> {
     __device__ static float ld1(const float *p) { return __ldg(p); }
 };
 
+// Loads of pixel data: through the read-only path (__ldg), or, for images another CTA
+// of the same launch may have written (CG), from L2 (__ldcg, coherent at the device
+// level once the writer's release has been observed).
+template <bool CG, typename V>
+__device__ __forceinline__ V ldx(const V *p)
+{
+    return CG ? __ldcg(p) : __ldg(p);
+}
+
+template <bool CG, typename T>
+__device__ __forceinline__ typename Pix<T>::Vec vld4(const T *p)
+{
+    return ldx<CG>(reinterpret_cast<const typename Pix<T>::Vec *>(p));
+}
+
 // raw loads of one row of both frames: 4 columns in each half + the column right of
 // the right half (used by lane 31 only); zero outside the image
 template <typename T> struct RawRow {
@@ -167,44 +182,47 @@ template <typename T> struct RawRow {
 
 // element loads with bounds checks; whole groups inside the row use one vector load
 // (vec: the rows allow it)
+template <bool CG>
 __device__ __forceinline__ uint32_t load4_checked(const unsigned char *row, int col, int W, bool rowok, int vec)
 {
-    if (vec && rowok && col + 4 <= W) return __ldg(reinterpret_cast<const unsigned int *>(row + col));
+    if (vec && rowok && col + 4 <= W) return ldx<CG>(reinterpret_cast<const unsigned int *>(row + col));
     uint32_t w = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool ok = rowok && col + k < W;
-        const uint32_t v = __ldg(row + (ok ? col + k : 0));
+        const uint32_t v = ldx<CG>(row + (ok ? col + k : 0));
         w |= (ok ? v : 0u) << (8 * k);
     }
     return w;
 }
+template <bool CG>
 __device__ __forceinline__ uint2 load4_checked(const unsigned short *row, int col, int W, bool rowok, int vec)
 {
-    if (vec && rowok && col + 4 <= W) return __ldg(reinterpret_cast<const uint2 *>(row + col));
+    if (vec && rowok && col + 4 <= W) return ldx<CG>(reinterpret_cast<const uint2 *>(row + col));
     uint32_t v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool ok = rowok && col + k < W;
-        const uint32_t x = __ldg(row + (ok ? col + k : 0));
+        const uint32_t x = ldx<CG>(row + (ok ? col + k : 0));
         v[k] = ok ? x : 0u;
     }
     return make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
 }
+template <bool CG>
 __device__ __forceinline__ float4 load4_checked(const float *row, int col, int W, bool rowok, int vec)
 {
-    if (vec && rowok && col + 4 <= W) return __ldg(reinterpret_cast<const float4 *>(row + col));
+    if (vec && rowok && col + 4 <= W) return ldx<CG>(reinterpret_cast<const float4 *>(row + col));
     float v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool ok = rowok && col + k < W;
-        const float x = __ldg(row + (ok ? col + k : 0));
+        const float x = ldx<CG>(row + (ok ? col + k : 0));
         v[k] = ok ? x : 0.f;
     }
     return make_float4(v[0], v[1], v[2], v[3]);
 }
 
-template <typename T, bool ROWCHK, bool COLCHK, bool VEC>
+template <typename T, bool ROWCHK, bool COLCHK, bool VEC, bool CG = false>
 __device__ __forceinline__ void load_raw(const PassParams &p, const T *fa, const T *fb, int gy, int gcl, RawRow<T> &r)
 {
     const bool rowok = !ROWCHK || gy < p.H;
@@ -215,22 +233,22 @@ __device__ __forceinline__ void load_raw(const PassParams &p, const T *fa, const
     const int gcr = gcl + HALF;
     if (!COLCHK && VEC) {
         const typename Pix<T>::Vec z = Pix<T>::zero();
-        const typename Pix<T>::Vec al = Pix<T>::ld4(ra + gcl), ar = Pix<T>::ld4(ra + gcr);
-        const typename Pix<T>::Vec bl = Pix<T>::ld4(rb + gcl), br = Pix<T>::ld4(rb + gcr);
+        const typename Pix<T>::Vec al = vld4<CG>(ra + gcl), ar = vld4<CG>(ra + gcr);
+        const typename Pix<T>::Vec bl = vld4<CG>(rb + gcl), br = vld4<CG>(rb + gcr);
         r.al = rowok ? al : z;
         r.ar = rowok ? ar : z;
         r.bl = rowok ? bl : z;
         r.br = rowok ? br : z;
     } else {
-        r.al = load4_checked(ra, gcl, p.W, rowok, p.vec);
-        r.ar = load4_checked(ra, gcr, p.W, rowok, p.vec);
-        r.bl = load4_checked(rb, gcl, p.W, rowok, p.vec);
-        r.br = load4_checked(rb, gcr, p.W, rowok, p.vec);
+        r.al = load4_checked<CG>(ra, gcl, p.W, rowok, p.vec);
+        r.ar = load4_checked<CG>(ra, gcr, p.W, rowok, p.vec);
+        r.bl = load4_checked<CG>(rb, gcl, p.W, rowok, p.vec);
+        r.br = load4_checked<CG>(rb, gcr, p.W, rowok, p.vec);
     }
     const int c4 = gcr + 4;
     const bool ok4 = rowok && (!COLCHK || c4 < p.W);
     const int c4c = ok4 ? c4 : 0;
-    const float va = Pix<T>::ld1(ra + c4c), vb = Pix<T>::ld1(rb + c4c);
+    const float va = (float)ldx<CG>(ra + c4c), vb = (float)ldx<CG>(rb + c4c);
     r.a4 = ok4 ? va : 0.f;
     r.b4 = ok4 ? vb : 0.f;
 }
@@ -426,7 +444,7 @@ __device__ __forceinline__ void store_next(unsigned char *img, int64_t pitch, in
 
 // R0, C0: first cube row / column the tile reads; cubes outside [ilo, ihi) x [jlo, jhi)
 // are masked (MASK only)
-template <typename Tin, typename Tout, bool ROWCHK, bool COLCHK, bool MASK, bool WRITE, int RPW>
+template <typename Tin, typename Tout, bool ROWCHK, bool COLCHK, bool MASK, bool WRITE, int RPW, bool CG = false>
 __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, const Tin *fb, int pair, int R0,
                                           int C0, int ilo, int ihi, int jlo, int jhi, float2 acc[NSUM])
 {
@@ -438,15 +456,17 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
     // consecutive pairs of a video share frames (frame t+1 of pair t is frame t+1 of
     // the next pair): the first frame is written by pair 0 only; independent pairs
     // own two frames each
-    const bool wprev = WRITE && (p.write_prev == 1 || (p.write_prev == 0 && pair == 0));
+    // a descriptor with no next-level image (the last level) writes nothing, whatever WRITE
+    const bool wr = WRITE && (p.next != nullptr || p.next_cur != nullptr);
+    const bool wprev = wr && p.next != nullptr && (p.write_prev == 1 || (p.write_prev == 0 && pair == 0));
     const int64_t fprev = p.write_prev == 1 ? 2 * (int64_t)pair : (int64_t)pair;
-    unsigned char *nprev = WRITE && wprev ? p.next + fprev * p.next_fstride : nullptr;
-    unsigned char *ncur = WRITE ? (p.next_cur ? p.next_cur : p.next + (fprev + 1) * p.next_fstride) : nullptr;
+    unsigned char *nprev = wprev ? p.next + fprev * p.next_fstride : nullptr;
+    unsigned char *ncur = wr ? (p.next_cur ? p.next_cur : p.next + (fprev + 1) * p.next_fstride) : nullptr;
 
     constexpr int PF = COLCHK ? 1 : (FT_TTC_PF < RPW ? FT_TTC_PF : RPW);
     RawRow<Tin> raw[RPW + 1];
 #pragma unroll
-    for (int r = 0; r < PF; ++r) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r, gcl, raw[r]);
+    for (int r = 0; r < PF; ++r) load_raw<Tin, ROWCHK, COLCHK, !COLCHK, CG>(p, fa, fb, gr0 + r, gcl, raw[r]);
 
     float2 xk[4];
 #pragma unroll
@@ -456,13 +476,13 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
     Pyr py;
 #pragma unroll
     for (int r = 0; r <= RPW; ++r) {
-        if (r + PF <= RPW) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
+        if (r + PF <= RPW) load_raw<Tin, ROWCHK, COLCHK, !COLCHK, CG>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
         float2 A[4], D[4];
         const int i = gr0 + r - 1;
         row_step<Tin, MASK>(raw[r], lane, st, r == 0, xk, y, i >= ilo && i < ihi, gcl, gcl + HALF, jlo, jhi, acc,
                             A, D);
         y = add2(y, make_float2(1.f, 1.f));
-        if (WRITE && r < RPW) {
+        if (wr && r < RPW) {
             if ((r & 1) == 0) {
                 pyr_even(py, A, D);
             } else {
