@@ -505,6 +505,20 @@ ft_status ttc_server_remove(ttc_server *srv, int stream_id);
 ft_status ttc_server_submit(ttc_server *srv, int stream_id, const void *frame, int64_t pitch_bytes, int64_t seq,
                             double t_arrival);
 ft_status ttc_server_step(ttc_server *srv, int wait, ttc_served *done, int max_done, int *n_done);
+
+/*
+ * Load generator for measuring the serving runtime (no counterpart in the paper): keeps
+ * each of the nstreams admitted streams `ids` supplied with a waiting frame, taken in turn
+ * from its nframes host frames (frames[i * nframes + k], row pitch pitches[i]; page-locked
+ * memory lets the uploads run asynchronously), and steps the server until `pairs` results
+ * (FT_SERVED_RESULT) have come back.  Every tick then carries one pair per stream, so the
+ * rate is set by the runtime and the device rather than by the caller.  Reports are
+ * consumed; *seconds (wall clock), *served, *p50_ms and *p99_ms (submission to report)
+ * are written when non-null.  Errors: FT_ERR_INVALID_ARG, and those of submit and step.
+ */
+ft_status ttc_server_drive(ttc_server *srv, const int *ids, int nstreams, const void *const *frames,
+                           const int64_t *pitches, int nframes, int64_t pairs, double *seconds, int64_t *served,
+                           double *p50_ms, double *p99_ms);
 int ttc_server_in_flight(const ttc_server *srv);        /* ticks in flight */
 int64_t ttc_server_ticks(const ttc_server *srv);        /* ticks launched so far */
 int ttc_server_waiting(const ttc_server *srv, int stream_id);   /* the stream's waiting frames; all waiting

@@ -181,6 +181,11 @@ def load(path: Optional[str] = None):
     L.ttc_server_submit.restype = st
     L.ttc_server_step.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.ttc_server_step.restype = st
+    L.ttc_server_drive.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(_vp), _i64p,
+                                   ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]
+    L.ttc_server_drive.restype = st
     L.ttc_server_in_flight.argtypes = [_vp]
     L.ttc_server_in_flight.restype = ctypes.c_int
     L.ttc_server_ticks.argtypes = [_vp]
@@ -575,7 +580,8 @@ class TtcContext:
 
     @property
     def last_launch_count(self) -> int:
-        """Kernels launched by the last partial-sums stage (the merge/solve adds one)."""
+        """Kernels launched by the last solve, sequence or partial-sums call (a
+        ttc_reduce_solve after ttc_partial_sums adds one)."""
         return int(load().ttc_ctx_last_launch_count(self._h))
 
     def new_results(self, n: int) -> torch.Tensor:

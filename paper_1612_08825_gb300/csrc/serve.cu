@@ -14,6 +14,7 @@
 // other; with three frame slots per stream, the slot a tick uploads into was last read
 // by a tick that has completed.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <deque>
 #include <new>
@@ -385,3 +386,55 @@ extern "C" int ttc_server_waiting(const ttc_server *s, int id)
 extern "C" int64_t ttc_server_bytes_in_use(const ttc_server *s) { return s ? s->used : 0; }
 
 extern "C" int ttc_server_launches(const ttc_server *s) { return s && s->ctx ? ttc_ctx_last_launch_count(s->ctx) : 0; }
+
+// Load generator (measurement of the runtime, no counterpart in the paper): every listed
+// stream always has a frame waiting, taken in turn from its nframes host frames, and the
+// server is stepped until `pairs` results have come back.  Each tick therefore carries one
+// pair per stream, and the rate is that of the runtime and the device, not of the caller.
+extern "C" ft_status ttc_server_drive(ttc_server *s, const int *ids, int nstreams, const void *const *frames,
+                                      const int64_t *pitches, int nframes, int64_t pairs, double *seconds,
+                                      int64_t *served, double *p50_ms, double *p99_ms)
+{
+    if (!s || !ids || !frames || !pitches || nstreams < 1 || nframes < 1 || pairs < 1) return FT_ERR_INVALID_ARG;
+    for (int i = 0; i < nstreams; ++i)
+        if (ids[i] < 0 || ids[i] >= (int)s->streams.size() || !s->streams[(size_t)ids[i]].open)
+            return FT_ERR_INVALID_ARG;
+    using clk = std::chrono::steady_clock;
+    const clk::time_point t0 = clk::now();
+    auto now = [&] { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    std::vector<int64_t> next((size_t)nstreams, 0);
+    std::vector<double> lat;
+    lat.reserve((size_t)pairs);
+    std::vector<ttc_served> done((size_t)std::max(64, 2 * nstreams));
+    int64_t got = 0;
+    while (got < pairs) {
+        for (int i = 0; i < nstreams; ++i) {
+            if (ttc_server_waiting(s, ids[i]) > 0) continue;
+            const int64_t q = next[(size_t)i]++;
+            const ft_status st = ttc_server_submit(s, ids[i], frames[(size_t)i * nframes + (size_t)(q % nframes)],
+                                                   pitches[i], q, now());
+            if (st != FT_OK) return st;
+        }
+        int n = 0;
+        const ft_status st = ttc_server_step(s, 1, done.data(), (int)done.size(), &n);
+        if (st != FT_OK) return st;
+        const double t = now();
+        for (int k = 0; k < n; ++k)
+            if (done[(size_t)k].status == FT_SERVED_RESULT) {
+                lat.push_back(1e3 * (t - done[(size_t)k].t_arrival));
+                ++got;
+            }
+    }
+    if (seconds) *seconds = now();
+    if (served) *served = got;
+    auto pct = [&](double q) {
+        std::vector<double> v(lat);
+        const size_t k = std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5));
+        std::nth_element(v.begin(), v.begin() + (std::ptrdiff_t)k, v.end());
+        return v[k];
+    };
+    if (p50_ms) *p50_ms = lat.empty() ? 0.0 : pct(0.5);
+    if (p99_ms) *p99_ms = lat.empty() ? 0.0 : pct(0.99);
+    return FT_OK;
+}
+

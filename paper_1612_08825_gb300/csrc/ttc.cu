@@ -569,9 +569,13 @@ cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs
 // independent = 0 for the consecutive pairs of a video (frame t+1 shared)
 // the levels kernel takes levels 1 .. L-1 in one launch when their images have one pixel
 // type: uint16 (uint8 frames, at most 5 levels) or float (float frames)
+#ifndef FT_FUSE_LEVELS
+#define FT_FUSE_LEVELS 1        // 0: one launch per level and a separate merge/solve launch
+#endif
+
 bool levels_kernel_fits(int dtype, int levels)
 {
-    return levels >= 2 && (dtype == FT_F32 || levels <= 5);
+    return FT_FUSE_LEVELS && levels >= 2 && (dtype == FT_F32 || levels <= 5);
 }
 
 // merge + solve requested from launch_partials (fused into the levels kernel)
@@ -784,6 +788,18 @@ extern "C" ft_status ttc_reduce_solve(ttc_ctx *ctx, int mode, ttc_level_result *
     return launch_solve(ctx, mode, out, ft::as_stream(stream));
 }
 
+namespace {
+
+// the merge + solve as its own launch (when the levels kernel did not run it)
+ft_status solve_after(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream_t s)
+{
+    const ft_status st = launch_solve(ctx, mode, out, s);
+    if (st == FT_OK) ++ctx->launches;
+    return st;
+}
+
+}  // namespace
+
 extern "C" ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, int dtype, int H, int W,
                                int64_t pitch_bytes, int levels, int mode, ttc_level_result *out,
                                void *stream)
@@ -795,7 +811,7 @@ extern "C" ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, 
     ft_status st = launch_partials(ctx, prev, cur, 0, 1, 0, dtype, H, W, pitch_bytes, levels,
                                    ft::as_stream(stream), 0, &req, &solved);
     if (st != FT_OK || solved) return st;
-    return launch_solve(ctx, mode, out, ft::as_stream(stream));
+    return solve_after(ctx, mode, out, ft::as_stream(stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -1308,7 +1324,7 @@ extern "C" ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_
     ft_status st = launch_partials(ctx, f0, f0 + frame_stride_bytes, frame_stride_bytes, T - 1, 0, dtype, H, W,
                                    pitch_bytes, levels, ft::as_stream(stream), 0, &req, &solved);
     if (st != FT_OK || solved) return st;
-    return launch_solve(ctx, mode, out, ft::as_stream(stream));
+    return solve_after(ctx, mode, out, ft::as_stream(stream));
 }
 
 namespace {

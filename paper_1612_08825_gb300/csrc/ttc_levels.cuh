@@ -77,8 +77,17 @@ __device__ __forceinline__ bool wait_count(const int *ctr, int need, const int *
 // inwards and mask (VAR 1); other edge tiles check every load (VAR 2).  A call, not
 // inlined, one per variant: each gets the registers of a standalone pass kernel, and the
 // persistent loop's state stays out of them.
-template <typename Tin, int RPW, int VAR>
-__device__ __noinline__ void level_tile(const PassParams &p, int pair, int ty, int tx, float *red, float *dst)
+#ifndef FT_LEVEL_TILE_CALL
+#define FT_LEVEL_TILE_CALL 1    // 0: tile bodies inlined into the persistent loop
+#endif
+#if FT_LEVEL_TILE_CALL
+#define FT_LEVEL_TILE_ATTR __noinline__
+#else
+#define FT_LEVEL_TILE_ATTR __forceinline__
+#endif
+
+template <typename Tin, int RPW, int VAR, bool CG>
+__device__ FT_LEVEL_TILE_ATTR void level_tile(const PassParams &p, int pair, int ty, int tx, float *red, float *dst)
 {
     constexpr int TRL = 8 * RPW;
     const int ilo = ty * TRL, jlo = tx * TC;
@@ -89,13 +98,13 @@ __device__ __noinline__ void level_tile(const PassParams &p, int pair, int ty, i
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc2[s] = make_float2(0.f, 0.f);
     if (VAR == 0) {
-        pass_body<Tin, Tin, false, false, false, true, RPW, true>(p, fa, fb, pair, ilo, jlo, ilo, ihi, jlo, jhi, acc2);
+        pass_body<Tin, Tin, false, false, false, true, RPW, CG>(p, fa, fb, pair, ilo, jlo, ilo, ihi, jlo, jhi, acc2);
     } else if (VAR == 1) {
         const int R0 = min(ilo, (p.H - 1 - TRL + 1) & ~1);
         const int C0 = min(jlo, (p.W - 1 - TC + 3) & ~3);
-        pass_body<Tin, Tin, false, false, true, true, RPW, true>(p, fa, fb, pair, R0, C0, ilo, ihi, jlo, jhi, acc2);
+        pass_body<Tin, Tin, false, false, true, true, RPW, CG>(p, fa, fb, pair, R0, C0, ilo, ihi, jlo, jhi, acc2);
     } else {
-        pass_body<Tin, Tin, true, true, true, true, RPW, true>(p, fa, fb, pair, ilo, jlo, ilo, ihi, jlo, jhi, acc2);
+        pass_body<Tin, Tin, true, true, true, true, RPW, CG>(p, fa, fb, pair, ilo, jlo, ilo, ihi, jlo, jhi, acc2);
     }
     float acc[NSUM];
 #pragma unroll
@@ -103,15 +112,17 @@ __device__ __noinline__ void level_tile(const PassParams &p, int pair, int ty, i
     block_reduce(acc, red, dst);
 }
 
-template <typename Tin, int RPW>
+// CG: the level's images were written by this launch (levels >= 2): loads from L2.
+// Level 1 was written by the level-0 launch before, and reads through L1.
+template <typename Tin, int RPW, bool CG>
 __device__ __forceinline__ void level_tile_any(const PassParams &p, int pair, int ty, int tx, float *red, float *dst)
 {
     constexpr int TRL = 8 * RPW;
     const bool big = p.H >= TRL + 2 && p.W >= TC + 4;
     const bool edge = ty == p.tiles_y - 1 || tx == p.tiles_x - 1;
-    if (!edge && big) level_tile<Tin, RPW, 0>(p, pair, ty, tx, red, dst);
-    else if (p.padded && big) level_tile<Tin, RPW, 1>(p, pair, ty, tx, red, dst);
-    else level_tile<Tin, RPW, 2>(p, pair, ty, tx, red, dst);
+    if (!edge && big) level_tile<Tin, RPW, 0, CG>(p, pair, ty, tx, red, dst);
+    else if (p.padded && big) level_tile<Tin, RPW, 1, CG>(p, pair, ty, tx, red, dst);
+    else level_tile<Tin, RPW, 2, CG>(p, pair, ty, tx, red, dst);
 }
 
 // the pair's every level is done: merge and solve, one warp per level (a call, not
@@ -119,7 +130,6 @@ __device__ __forceinline__ void level_tile_any(const PassParams &p, int pair, in
 template <bool VIDEO>
 __device__ __noinline__ void solve_pair(const LevelsParams &lp, int pair)
 {
-    __threadfence();
     const int w = threadIdx.x >> 5;
     if (w >= lp.levels || pair < lp.skip) return;
     if (VIDEO) {
@@ -175,20 +185,30 @@ ttc_levels_kernel(const __grid_constant__ LevelsParams lp)
             }
             sh_ok = ok;
         }
+        // the acquire loads of thread 0 and this barrier order every later read of the
+        // CTA after the writes the counts stand for
         __syncthreads();
-        __threadfence();
         if (sh_ok) {
             const int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
             float *dst = p.partials + ((int64_t)dpair * p.ntiles + tile) * NSUM;
-            if (lp.rpw[l] == 8) level_tile_any<Tin, 8>(p, dpair, ty, tx, red, dst);
-            else level_tile_any<Tin, 2>(p, dpair, ty, tx, red, dst);
+            if (l == 1) {
+                if (lp.rpw[l] == 8) level_tile_any<Tin, 8, false>(p, dpair, ty, tx, red, dst);
+                else level_tile_any<Tin, 2, false>(p, dpair, ty, tx, red, dst);
+            } else {
+                if (lp.rpw[l] == 8) level_tile_any<Tin, 8, true>(p, dpair, ty, tx, red, dst);
+                else level_tile_any<Tin, 2, true>(p, dpair, ty, tx, red, dst);
+            }
         }
-        // every write of this item (next-level pixels, partials) before the count
-        __threadfence();
+        // every write of this item (next-level pixels, partials) before the count: the
+        // barrier, then one thread's device-scope fence (cumulative over the writes the
+        // barrier ordered before it) and the count
         __syncthreads();
         if (tid == 0) {
+            __threadfence();
             const int old = atomicAdd(lp.done + (int64_t)l * lp.npairs + pair, 1);
             sh_last = lp.solve && l == lp.levels - 1 && old + 1 == p.ntiles;
+            // the pair's last count: every other item's writes are visible from here on
+            if (sh_last) __threadfence();
             sh_t = tn;
         }
         __syncthreads();

@@ -126,22 +126,37 @@ __device__ __forceinline__ float b256(uint32_t w, uint32_t k)
     return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7604u | (k << 4)));
 }
 
-// raw bytes of one row of both frames: 4 columns in each half, and the first 4 columns
-// of the extra box (column 256 of the tile: the right neighbour of lane 31's right half)
+// raw bytes of one row of both frames: 4 columns in each half, and the right
+// neighbour of lane 31's columns in byte 0 of xa / xb (column 256 of the tile: the
+// first column of the extra box).  Folded tiles (see tile_body) pair row i with row
+// i + 32 of the same columns instead; lane 31's neighbours are then column 128 of those
+// two rows (bytes 0 and 1 of xa / xb).
 struct Raw8 {
     uint32_t al, ar, bl, br, xa, xb;
 };
 
 // one row of both frames for this thread, from the tile buffer (pixel row `row`)
+template <bool FOLD>
 __device__ __forceinline__ void row_from_smem(const unsigned char *buf, int row, int lane, Raw8 &r)
 {
     const unsigned char *fa = buf, *fb = buf + FRAME;
     r.al = *reinterpret_cast<const uint32_t *>(fa + row * BW + 4 * lane);
-    r.ar = *reinterpret_cast<const uint32_t *>(fa + BOX + row * BW + 4 * lane);
     r.bl = *reinterpret_cast<const uint32_t *>(fb + row * BW + 4 * lane);
-    r.br = *reinterpret_cast<const uint32_t *>(fb + BOX + row * BW + 4 * lane);
-    r.xa = *reinterpret_cast<const uint32_t *>(fa + 2 * BOX + row * XW);
-    r.xb = *reinterpret_cast<const uint32_t *>(fb + 2 * BOX + row * XW);
+    if (FOLD) {
+        r.ar = *reinterpret_cast<const uint32_t *>(fa + (row + 32) * BW + 4 * lane);
+        r.br = *reinterpret_cast<const uint32_t *>(fb + (row + 32) * BW + 4 * lane);
+        const uint32_t a0 = *reinterpret_cast<const uint32_t *>(fa + BOX + row * BW);
+        const uint32_t a1 = *reinterpret_cast<const uint32_t *>(fa + BOX + (row + 32) * BW);
+        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(fb + BOX + row * BW);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(fb + BOX + (row + 32) * BW);
+        r.xa = __byte_perm(a0, a1, 0x0040u);
+        r.xb = __byte_perm(b0, b1, 0x0040u);
+    } else {
+        r.ar = *reinterpret_cast<const uint32_t *>(fa + BOX + row * BW + 4 * lane);
+        r.br = *reinterpret_cast<const uint32_t *>(fb + BOX + row * BW + 4 * lane);
+        r.xa = *reinterpret_cast<const uint32_t *>(fa + 2 * BOX + row * XW);
+        r.xb = *reinterpret_cast<const uint32_t *>(fb + 2 * BOX + row * XW);
+    }
 }
 
 // The previous row's contribution to the cubes between it and the next row, per
@@ -156,9 +171,9 @@ struct Strip8 {
 // (the 2x2x2 first differences of Sec. II, times 4 * 256), G and the ten products.
 // The neighbour column's s and d come from lane+1 (lane 31 of the right half: the
 // extra box).  Returns the row's scaled pixels of both frames for the pyramid.
-template <bool MASK>
+template <bool MASK, bool FOLD>
 __device__ __forceinline__ void row_step8(const Raw8 &r, int lane, Strip8 &st, bool first, const float2 xk[4],
-                                          float2 y, bool rowok, int jl, int jr, int jlo, int jhi,
+                                          float2 y, bool rowok_l, bool rowok_r, int jl, int jr, int jlo, int jhi,
                                           float2 acc[NSUM], float2 A[4], float2 B[4])
 {
     float2 s[5], d[5];
@@ -175,8 +190,14 @@ __device__ __forceinline__ void row_step8(const Raw8 &r, int lane, Strip8 &st, b
     const float s4r = __shfl_sync(0xffffffffu, s[0].y, src);
     const float d4r = __shfl_sync(0xffffffffu, d[0].y, src);
     const float xa = b256(r.xa, 0), xb = b256(r.xb, 0);
-    s[4] = make_float2(s4l, lane == 31 ? xa + xb : s4r);
-    d[4] = make_float2(d4l, lane == 31 ? xb - xa : d4r);
+    if (FOLD) {
+        const float xa1 = b256(r.xa, 1), xb1 = b256(r.xb, 1);
+        s[4] = make_float2(lane == 31 ? xa + xb : s4l, lane == 31 ? xa1 + xb1 : s4r);
+        d[4] = make_float2(lane == 31 ? xb - xa : d4l, lane == 31 ? xb1 - xa1 : d4r);
+    } else {
+        s[4] = make_float2(s4l, lane == 31 ? xa + xb : s4r);
+        d[4] = make_float2(d4l, lane == 31 ? xb - xa : d4r);
+    }
     float2 hs[4], hp[4], dp[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -192,7 +213,7 @@ __device__ __forceinline__ void row_step8(const Raw8 &r, int lane, Strip8 &st, b
             float2 et = add2(dp[k], st.dp[k]);
             if (MASK) {
                 const int cl = jl + k, cr = jr + k;
-                mask3(ex, ey, et, rowok && cl >= jlo && cl < jhi, rowok && cr >= jlo && cr < jhi);
+                mask3(ex, ey, et, rowok_l && cl >= jlo && cl < jhi, rowok_r && cr >= jlo && cr < jhi);
             }
             accum2(acc, ex, ey, et, xk[k], y);
         }
@@ -223,14 +244,22 @@ __device__ __forceinline__ void store_u16(unsigned char *img, int64_t pitch, int
     else if (c < Wn) row[c] = (unsigned short)lo;
 }
 
-template <bool MASK, bool WRITE>
+// One tile of 64 x 256 cubes.  A thread's packed pair of lanes normally holds the same
+// 4 columns of the tile's left and right halves, and a warp walks 8 cube rows.  A tile
+// whose cubes all lie in the left half (FOLD: the last, narrow tile column of an image)
+// pairs each left-half row with the row 32 below it instead, so a warp walks 4 rows and
+// the tile costs about half.
+template <bool MASK, bool WRITE, bool FOLD>
 __device__ __forceinline__ void tile_body(const PassParams &p, const unsigned char *buf, int pair, int R0, int C0,
                                           float2 acc[NSUM])
 {
+    constexpr int RPW = FOLD ? 4 : 8;           // cube rows per warp
+    constexpr int DR = FOLD ? TR / 2 : 0;       // row offset of the pair's second lane
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gcl = C0 + 4 * lane;
-    const int gr0 = R0 + 8 * warp;
-    const float2 x0 = make_float2((float)gcl + p.xoff, (float)(gcl + HALF) + p.xoff);
+    const int gcr = FOLD ? gcl : gcl + HALF;    // columns of the pair's second lane
+    const int gr0 = R0 + RPW * warp;
+    const float2 x0 = make_float2((float)gcl + p.xoff, (float)gcr + p.xoff);
     const int Hn = p.H >> 1, Wn = p.W >> 1;
     const int ihi = min(R0 + TR, p.H - 1), jhi = min(C0 + TC, p.W - 1);
     // consecutive pairs of a video share frames: the first frame's next level is written
@@ -244,20 +273,21 @@ __device__ __forceinline__ void tile_body(const PassParams &p, const unsigned ch
     float2 xk[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) xk[k] = add2(x0, make_float2((float)k, (float)k));
-    float2 y = make_float2((float)(gr0 - 1) + p.yoff, (float)(gr0 - 1) + p.yoff);
+    float2 y = make_float2((float)(gr0 - 1) + p.yoff, (float)(gr0 - 1 + DR) + p.yoff);
     Strip8 st;
     float2 hb[2], ha[2];            // horizontal pair sums of the even row (cur, prev)
     Raw8 nxt;
-    row_from_smem(buf, 8 * warp, lane, nxt);
+    row_from_smem<FOLD>(buf, RPW * warp, lane, nxt);
 #pragma unroll
-    for (int r = 0; r < 9; ++r) {
+    for (int r = 0; r <= RPW; ++r) {
         const Raw8 cur = nxt;
-        if (r < 8) row_from_smem(buf, 8 * warp + r + 1, lane, nxt);
+        if (r < RPW) row_from_smem<FOLD>(buf, RPW * warp + r + 1, lane, nxt);
         float2 A[4], B[4];
         const int i = gr0 + r - 1;
-        row_step8<MASK>(cur, lane, st, r == 0, xk, y, i >= R0 && i < ihi, gcl, gcl + HALF, C0, jhi, acc, A, B);
+        row_step8<MASK, FOLD>(cur, lane, st, r == 0, xk, y, i >= R0 && i < ihi, i + DR >= R0 && i + DR < ihi, gcl,
+                              gcr, C0, jhi, acc, A, B);
         y = add2(y, make_float2(1.f, 1.f));
-        if (WRITE && r < 8) {
+        if (WRITE && r < RPW) {
             const float2 b0 = add2(B[0], B[1]), b1 = add2(B[2], B[3]);
             float2 a0, a1;
             if (wprev) {
@@ -272,15 +302,15 @@ __device__ __forceinline__ void tile_body(const PassParams &p, const unsigned ch
                     ha[1] = a1;
                 }
             } else {
-                const int r1 = (gr0 >> 1) + (r >> 1);
-                const int cl = gcl >> 1, cr = (gcl + HALF) >> 1;
+                const int r1 = (gr0 >> 1) + (r >> 1), r2 = r1 + DR / 2;
+                const int cl = gcl >> 1, cr = gcr >> 1;
                 const float2 v0 = unscale_block(add2(hb[0], b0)), v1 = unscale_block(add2(hb[1], b1));
                 store_u16<MASK>(ncur, p.next_pitch, r1, cl, v0.x, v1.x, Hn, Wn);
-                store_u16<MASK>(ncur, p.next_pitch, r1, cr, v0.y, v1.y, Hn, Wn);
+                store_u16<MASK>(ncur, p.next_pitch, r2, cr, v0.y, v1.y, Hn, Wn);
                 if (wprev) {
                     const float2 u0 = unscale_block(add2(ha[0], a0)), u1 = unscale_block(add2(ha[1], a1));
                     store_u16<MASK>(nprev, p.next_pitch, r1, cl, u0.x, u1.x, Hn, Wn);
-                    store_u16<MASK>(nprev, p.next_pitch, r1, cr, u0.y, u1.y, Hn, Wn);
+                    store_u16<MASK>(nprev, p.next_pitch, r2, cr, u0.y, u1.y, Hn, Wn);
                 }
             }
         }
@@ -342,8 +372,10 @@ ttc_pass_tma_kernel(const __grid_constant__ Items items, int *status, unsigned e
 #pragma unroll
         for (int s = 0; s < NSUM; ++s) acc2[s] = make_float2(0.f, 0.f);
         const bool edge = (l.R0 + TR > p.H - 1) || (l.C0 + TC > p.W - 1);
-        if (edge) tile_body<true, WRITE>(p, bufs + b * BUF, l.pair, l.R0, l.C0, acc2);
-        else tile_body<false, WRITE>(p, bufs + b * BUF, l.pair, l.R0, l.C0, acc2);
+        const bool fold = p.W - 1 - l.C0 <= HALF;          // every cube in the left half
+        if (fold) tile_body<true, WRITE, true>(p, bufs + b * BUF, l.pair, l.R0, l.C0, acc2);
+        else if (edge) tile_body<true, WRITE, false>(p, bufs + b * BUF, l.pair, l.R0, l.C0, acc2);
+        else tile_body<false, WRITE, false>(p, bufs + b * BUF, l.pair, l.R0, l.C0, acc2);
         float acc[NSUM];
 #pragma unroll
         for (int s = 0; s < NSUM; ++s) acc[s] = acc2[s].x + acc2[s].y;

@@ -570,6 +570,26 @@ class NativeServer:
             out += self.step(block=True)
         return out
 
+    def drive(self, frames: Dict[int, list], pairs: int) -> dict:
+        """The library's load generator (ttc_server_drive): every stream in `frames`
+        (sid -> list of host frames of its size, cycled) always has a frame waiting; the
+        server is stepped natively until `pairs` results are back.  Returns seconds,
+        pairs served and p50 / p99 latency (ms, submission to report)."""
+        ct = self._ct
+        sids = list(frames)
+        nf = len(frames[sids[0]])
+        if any(len(frames[s]) != nf for s in sids):
+            raise ValueError("every stream gives the same number of frames")
+        ids = (ct.c_int * len(sids))(*[self.streams[s].nid for s in sids])
+        ptrs = (ct.c_void_p * (len(sids) * nf))(*[f.data_ptr() for s in sids for f in frames[s]])
+        pitches = (ct.c_int64 * len(sids))(*[frames[s][0].stride(0) * frames[s][0].element_size() for s in sids])
+        sec, got = ct.c_double(0), ct.c_int64(0)
+        p50, p99 = ct.c_double(0), ct.c_double(0)
+        self._check(self._L.ttc_server_drive(self._h, ids, len(sids), ptrs, pitches, nf, int(pairs), ct.byref(sec),
+                                             ct.byref(got), ct.byref(p50), ct.byref(p99)), "ttc_server_drive")
+        self.stats["ticks"] = int(self._L.ttc_server_ticks(self._h))
+        return {"seconds": sec.value, "pairs": int(got.value), "p50_ms": p50.value, "p99_ms": p99.value}
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._L.ttc_server_destroy(self._h)

@@ -257,3 +257,22 @@ def test_native_server_replay_and_saturate():
     saturate(srv, lambda s, q: frames[s][q % 3], ticks=6)
     assert srv.stats["results"] - n0 >= 5 * len(STREAMS)
     srv.close()
+
+
+def test_native_load_generator():
+    """ttc_server_drive keeps every stream supplied and returns at least the pairs asked
+    for, with latencies; the server then still serves frames offered the ordinary way."""
+    frames = {sid: _video(H, W, 3, 1200 + sid).pin_memory() for sid, H, W in STREAMS}
+    srv = NativeServer(1080, 1920, LEVELS, 40 << 30, max_batch=8, rows_per_tile=PLAN)
+    for sid, H, W in STREAMS:
+        assert srv.admit(sid, H, W)
+    r = srv.drive({sid: list(frames[sid]) for sid, *_ in STREAMS}, pairs=10 * len(STREAMS))
+    assert r["pairs"] >= 10 * len(STREAMS) and r["seconds"] > 0
+    assert 0 < r["p50_ms"] <= r["p99_ms"]
+    for sid, H, W in STREAMS:
+        assert srv.offer(Frame(sid, 10 ** 6, 0.0, frames[sid][0]))
+    res = [c for c in srv.drain() if c.records is not None]
+    assert sorted(c.stream for c in res) == sorted(sid for sid, *_ in STREAMS)
+    for c in res:
+        assert c.records.shape[0] == LEVELS and np.all(c.records["flags"] & ft.FLAG_TIMEOUT == 0)
+    srv.close()
