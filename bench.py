@@ -175,11 +175,27 @@ def run_reference(args):
 # our arm
 # --------------------------------------------------------------------------- #
 
+class L2Flush:
+    """Between timed launches: write a buffer larger than L2 (evicts the launch's inputs),
+    then read another one as large, so that the dirty lines of the write are written back
+    before the timed launch rather than during it; L2 is left holding clean lines of
+    neither the inputs nor the outputs."""
+
+    def __init__(self, dev):
+        import torch
+        self.w = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+        self.r = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def __call__(self):
+        self.w.zero_()
+        self.r.sum()
+
+
 def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
     import torch
     import paper_1612_08825_gb300 as ft
     import scenes
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     rows = []
     # the sweep's shapes, plus batches of 16 images (a leading extent-1 kernel axis)
     # that show the sustained rates: a single 1080p image is too small to fill the GPU
@@ -197,7 +213,7 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
         s = torch.cuda.current_stream(dev)
         times = []
         for i in range(reps + 2):
-            flush.zero_()
+            flush()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(s)
@@ -226,7 +242,7 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
         out = ft.fastconv_nd(E, k)
         ts = []
         for i in range(reps + 2):
-            flush.zero_()
+            flush()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(s)
@@ -257,7 +273,7 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
         for i in range(reps + 2):
             for fn, acc in ((lambda: ft.fastconv_nd(Ec, k, out=out), t_dir),
                             (lambda: plan(Ec, k, out=out, workspace=ws), t_fft)):
-                flush.zero_()
+                flush()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(s)
@@ -280,7 +296,7 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
     def timed(fn):
         ts = []
         for i in range(reps + 2):
-            flush.zero_()
+            flush()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(s)
@@ -327,7 +343,7 @@ def gradient_bench(dev, hbm_peak, reps):
     import torch
     import paper_1612_08825_gb300 as ft
     import scenes
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     rows = []
     sc = scenes.tilted_plane_scene(H=H, W=W, seed=5)
     img = scenes.render(sc, 0.0, device=dev)
@@ -339,7 +355,7 @@ def gradient_bench(dev, hbm_peak, reps):
         angs = torch.empty((n, H - 1, W - 1), device=dev)
         ts = []
         for i in range(reps + 2):
-            flush.zero_()
+            flush()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(s)

@@ -338,16 +338,18 @@ conv_fma_kernel(const ConvParams p)
     }
 }
 
-// Fallback for kernels too large for the tiled path: one thread per output element.
+// Fallback for kernels too large for the tiled path, and the last few output columns
+// of the streaming kernel: one thread per output element of the output columns
+// [col0, col0 + ncols) of every row (the kernel taps in the streaming kernel's order).
 __global__ void __launch_bounds__(kThreads)
-conv_direct_kernel(const ConvParams p, int64_t total)
+conv_direct_kernel(const ConvParams p, int64_t total, int64_t col0, int64_t ncols)
 {
     const int64_t o = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (o >= total) return;
-    const int64_t plane_size = p.Mr * p.Mc;
+    const int64_t plane_size = p.Mr * ncols;
     const int64_t plane = o / plane_size;
     const int64_t rem = o - plane * plane_size;
-    const int64_t oy = rem / p.Mc, ox = rem - oy * p.Mc;
+    const int64_t oy = rem / ncols, ox = col0 + (rem - oy * ncols);
     int64_t pm[FT_MAX_NDIM];
     {
         int64_t r = plane;
@@ -379,7 +381,7 @@ conv_direct_kernel(const ConvParams p, int64_t total)
             for (int64_t b = b_lo; b <= b_hi; ++b)
                 acc = fmaf(__ldg(kk + a * p.Kc + b), __ldg(src + (oy - a) * p.Nc + (ox - b)), acc);
     }
-    p.out[o] = acc;
+    p.out[(plane * p.Mr + oy) * p.Mc + ox] = acc;
 }
 
 // Streaming kernel for small kernels (memory-bound): one warp per 128-column strip
@@ -506,16 +508,25 @@ conv_rows_kernel(const ConvParams p, int64_t nstrips, int64_t nrb, int64_t total
     }
 }
 
+// An output row of 128 n + r columns with 1 <= r <= 8 (such as 257 or 1921) would give a
+// whole strip of warps for r columns: those columns are computed by the direct kernel
+// instead (same taps, same order), the strips cover the first 128 n.
 template <int KL, int KR, int KC>
 ft_status launch_rows(const ConvParams &p, int64_t planes, cudaStream_t s)
 {
     constexpr int RB = 8;
-    const int64_t nstrips = ft::ceil_div(p.Mc, 128);
+    const int64_t rem = p.Mc % 128;
+    const bool tail = p.Mc > 128 && rem >= 1 && rem <= 8;
+    const int64_t nstrips = tail ? p.Mc / 128 : ft::ceil_div(p.Mc, 128);
     const int64_t nrb = ft::ceil_div(p.Mr, RB);
     const int64_t warps = planes * nstrips * nrb;
     const int64_t blocks = ft::ceil_div(warps, kThreads / 32);
     if (blocks > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
     conv_rows_kernel<KL, KR, KC, RB><<<(unsigned)blocks, kThreads, 0, s>>>(p, nstrips, nrb, warps);
+    if (tail) {
+        const int64_t n = planes * p.Mr * rem;
+        conv_direct_kernel<<<(unsigned)ft::ceil_div(n, kThreads), kThreads, 0, s>>>(p, n, p.Mc - rem, rem);
+    }
     return ft::check_launch();
 }
 
@@ -696,7 +707,7 @@ static ft_status conv_nd_impl(const float *input, const int64_t *dims, int nd, c
     if (!tiled) {
         if (tot_out / 256 + 1 > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
         const unsigned blocks = (unsigned)ft::ceil_div(tot_out, kThreads);
-        conv_direct_kernel<<<blocks, kThreads, 0, s>>>(p, tot_out);
+        conv_direct_kernel<<<blocks, kThreads, 0, s>>>(p, tot_out, 0, p.Mc);
         return ft::check_launch();
     }
     // small kernels (at most 2 leading taps, plane kernel up to 3 x 3): memory-bound.

@@ -569,8 +569,12 @@ cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs
 // independent = 0 for the consecutive pairs of a video (frame t+1 shared)
 // the levels kernel takes levels 1 .. L-1 in one launch when their images have one pixel
 // type: uint16 (uint8 frames, at most 5 levels) or float (float frames)
+// Levels >= 1: one launch per level (tile sets of ttc_pass_kernel / ttc_batch_kernel)
+// and a merge/solve launch by default; 1: the persistent levels kernel
+// (ttc_levels.cuh), which measured slower on GB300 (1080p video, 299 pairs: 1.32 against
+// 1.09 ms per step; 512 uneven pairs: 1.27 against 1.11 ms per batch).
 #ifndef FT_FUSE_LEVELS
-#define FT_FUSE_LEVELS 1        // 0: one launch per level and a separate merge/solve launch
+#define FT_FUSE_LEVELS 0
 #endif
 
 bool levels_kernel_fits(int dtype, int levels)
