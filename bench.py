@@ -639,8 +639,9 @@ def accuracy(sc, res, levels):
 # sums of both frames: 6 adds per 4 level-0 pixels = 1.5)
 OPS_PER_CUBE0 = 23.5
 # DRAM bytes (read + write) of one level-0 launch over the 299 pairs, from an ncu capture
-# of the same kernel on an 80-frame video (3.82 MB per pair, scaled by pairs)
-L0_TRAFFIC_PER_PAIR = 3.82e6
+# of the same kernel on an 80-frame video (287.9 MB for 79 pairs: 3.64 MB per pair,
+# scaled by pairs)
+L0_TRAFFIC_PER_PAIR = 3.64e6
 
 
 def conv_hbm_summary(rows, hbm_peak):
