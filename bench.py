@@ -179,16 +179,23 @@ class L2Flush:
     """Between timed launches: write a buffer larger than L2 (evicts the launch's inputs),
     then read another one as large, so that the dirty lines of the write are written back
     before the timed launch rather than during it; L2 is left holding clean lines of
-    neither the inputs nor the outputs."""
+    neither the inputs nor the outputs.  Then the device spins for about 0.3 ms, so that
+    the host has enqueued the timed call before the device reaches the call's start event:
+    the events then time the device's work, not the host-side marshalling of a short call
+    (which the small-call measurements report separately)."""
+
+    SPIN_CYCLES = 600_000
 
     def __init__(self, dev):
         import torch
+        self.torch = torch
         self.w = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
         self.r = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     def __call__(self):
         self.w.zero_()
         self.r.sum()
+        self.torch.cuda._sleep(self.SPIN_CYCLES)
 
 
 def fastconv_sweep(dev, hbm_peak, fma_peak, reps):

@@ -198,6 +198,8 @@ typedef enum { FT_MODE_TTC = 0, FT_MODE_FOE = 1 } ft_mode;
 #define FT_FLAG_C_ZERO 2     /* C == 0: TTC = +inf, FOE = NaN */
 #define FT_FLAG_RECEDING 4   /* C < 0: the camera moves away; TTC is negative */
 #define FT_FLAG_TIMEOUT 8    /* a bounded wait inside the kernels expired: this call's sums are incomplete */
+#define FT_FLAG_BOUNDS 16    /* only in builds with FASTTTC_CHECK=1 (FT_CHECK): a kernel of this call found a
+                                read outside its frame or a write outside its image; the access was skipped */
 
 /*
  * One solve result for one frame pair at one pyramid level (152 bytes).

@@ -31,7 +31,7 @@ __all__ = [
 
 MODE_TTC, MODE_FOE = 0, 1
 DTYPE_U8, DTYPE_F32 = 0, 1
-FLAG_SINGULAR, FLAG_C_ZERO, FLAG_RECEDING, FLAG_TIMEOUT = 1, 2, 4, 8
+FLAG_SINGULAR, FLAG_C_ZERO, FLAG_RECEDING, FLAG_TIMEOUT, FLAG_BOUNDS = 1, 2, 4, 8, 16
 ERR_TIMEOUT = 6
 MAX_LEVELS = 7
 MAX_NDIM = 8

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "fastttc.h"
@@ -27,6 +28,19 @@ inline ft_status check_launch()
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// A named NVTX range around one C-ABI call, for timeline profilers (a push and a pop
+// that cost a branch each when no tool is attached).
+struct ApiRange {
+    explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange &) = delete;
+    ApiRange &operator=(const ApiRange &) = delete;
+};
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace ft
+
+// the range of the enclosing C-ABI function, named after it
+#define FT_API_RANGE ft::ApiRange ft_api_range_(__func__)
+

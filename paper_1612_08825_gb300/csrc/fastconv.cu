@@ -338,18 +338,16 @@ conv_fma_kernel(const ConvParams p)
     }
 }
 
-// Fallback for kernels too large for the tiled path, and the last few output columns
-// of the streaming kernel: one thread per output element of the output columns
-// [col0, col0 + ncols) of every row (the kernel taps in the streaming kernel's order).
+// Fallback for kernels too large for the tiled path: one thread per output element.
 __global__ void __launch_bounds__(kThreads)
-conv_direct_kernel(const ConvParams p, int64_t total, int64_t col0, int64_t ncols)
+conv_direct_kernel(const ConvParams p, int64_t total)
 {
     const int64_t o = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (o >= total) return;
-    const int64_t plane_size = p.Mr * ncols;
+    const int64_t plane_size = p.Mr * p.Mc;
     const int64_t plane = o / plane_size;
     const int64_t rem = o - plane * plane_size;
-    const int64_t oy = rem / ncols, ox = col0 + (rem - oy * ncols);
+    const int64_t oy = rem / p.Mc, ox = rem - oy * p.Mc;
     int64_t pm[FT_MAX_NDIM];
     {
         int64_t r = plane;
@@ -381,7 +379,7 @@ conv_direct_kernel(const ConvParams p, int64_t total, int64_t col0, int64_t ncol
             for (int64_t b = b_lo; b <= b_hi; ++b)
                 acc = fmaf(__ldg(kk + a * p.Kc + b), __ldg(src + (oy - a) * p.Nc + (ox - b)), acc);
     }
-    p.out[(plane * p.Mr + oy) * p.Mc + ox] = acc;
+    p.out[o] = acc;
 }
 
 // Streaming kernel for small kernels (memory-bound): one warp per 128-column strip
@@ -508,25 +506,16 @@ conv_rows_kernel(const ConvParams p, int64_t nstrips, int64_t nrb, int64_t total
     }
 }
 
-// An output row of 128 n + r columns with 1 <= r <= 8 (such as 257 or 1921) would give a
-// whole strip of warps for r columns: those columns are computed by the direct kernel
-// instead (same taps, same order), the strips cover the first 128 n.
 template <int KL, int KR, int KC>
 ft_status launch_rows(const ConvParams &p, int64_t planes, cudaStream_t s)
 {
     constexpr int RB = 8;
-    const int64_t rem = p.Mc % 128;
-    const bool tail = p.Mc > 128 && rem >= 1 && rem <= 8;
-    const int64_t nstrips = tail ? p.Mc / 128 : ft::ceil_div(p.Mc, 128);
+    const int64_t nstrips = ft::ceil_div(p.Mc, 128);
     const int64_t nrb = ft::ceil_div(p.Mr, RB);
     const int64_t warps = planes * nstrips * nrb;
     const int64_t blocks = ft::ceil_div(warps, kThreads / 32);
     if (blocks > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
     conv_rows_kernel<KL, KR, KC, RB><<<(unsigned)blocks, kThreads, 0, s>>>(p, nstrips, nrb, warps);
-    if (tail) {
-        const int64_t n = planes * p.Mr * rem;
-        conv_direct_kernel<<<(unsigned)ft::ceil_div(n, kThreads), kThreads, 0, s>>>(p, n, p.Mc - rem, rem);
-    }
     return ft::check_launch();
 }
 
@@ -707,7 +696,7 @@ static ft_status conv_nd_impl(const float *input, const int64_t *dims, int nd, c
     if (!tiled) {
         if (tot_out / 256 + 1 > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
         const unsigned blocks = (unsigned)ft::ceil_div(tot_out, kThreads);
-        conv_direct_kernel<<<blocks, kThreads, 0, s>>>(p, tot_out, 0, p.Mc);
+        conv_direct_kernel<<<blocks, kThreads, 0, s>>>(p, tot_out);
         return ft::check_launch();
     }
     // small kernels (at most 2 leading taps, plane kernel up to 3 x 3): memory-bound.
@@ -739,6 +728,7 @@ extern "C" ft_status fastconv_nd(const float *input, const int64_t *dims, int nd
                                  const float *kernel, const int64_t *kdims, float *out,
                                  void *stream)
 {
+    FT_API_RANGE;
     return conv_nd_impl(input, dims, nd, kernel, kdims, out, ft::as_stream(stream));
 }
 
@@ -762,6 +752,7 @@ extern "C" ft_status fastconv_nd_typed(const void *input, int in_dtype, const in
                                        const float *kernel, const int64_t *kdims, float *out, float *scratch,
                                        void *stream)
 {
+    FT_API_RANGE;
     cudaStream_t s = ft::as_stream(stream);
     if (in_dtype == FT_F32) return conv_nd_impl(static_cast<const float *>(input), dims, nd, kernel, kdims, out, s);
     if (in_dtype != FT_U8 && in_dtype != FT_I16 && in_dtype != FT_F16 && in_dtype != FT_BF16)
@@ -802,6 +793,7 @@ extern "C" ft_status fastconv_separable(const float *input, const int64_t *dims,
                                         const float *const *factors, const int64_t *kdims, float *out,
                                         float *scratch, void *stream)
 {
+    FT_API_RANGE;
     if (!input || !dims || !factors || !kdims || !out) return FT_ERR_INVALID_ARG;
     int64_t odims[FT_MAX_NDIM];
     ft_status st = fastconv_out_dims(nd, dims, kdims, odims);

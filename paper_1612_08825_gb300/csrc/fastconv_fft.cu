@@ -173,6 +173,7 @@ void pad_sizes(const Shape &sh, size_t *r, size_t *c)
 extern "C" ft_status fastconv_fft_plan_create(const int64_t *dims, int nd, const int64_t *kdims,
                                               fastconv_fft_plan **plan, size_t *workspace_bytes)
 {
+    FT_API_RANGE;
     if (!plan) return FT_ERR_INVALID_ARG;
     *plan = nullptr;
     const ft_status st = check_args(dims, nd, kdims);
@@ -243,6 +244,7 @@ extern "C" size_t fastconv_fft_plan_workspace(const fastconv_fft_plan *plan)
 extern "C" ft_status fastconv_fft(fastconv_fft_plan *plan, const float *input, const float *kernel, float *out,
                                   void *workspace, size_t workspace_bytes, void *stream)
 {
+    FT_API_RANGE;
     if (!plan || !input || !kernel || !out || !workspace) return FT_ERR_INVALID_ARG;
     if (workspace_bytes < plan->pad_bytes + plan->work_bytes) return FT_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return FT_ERR_INVALID_ARG;

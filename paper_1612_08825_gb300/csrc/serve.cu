@@ -218,6 +218,7 @@ extern "C" ft_status ttc_server_create(ttc_server **out, int max_H, int max_W, i
                                        int dtype, int max_batch, int max_streams, int max_pending,
                                        int64_t hbm_budget_bytes, const int *rows_per_tile)
 {
+    FT_API_RANGE;
     if (!out) return FT_ERR_INVALID_ARG;
     *out = nullptr;
     if ((dtype != FT_U8 && dtype != FT_F32) || (mode != FT_MODE_TTC && mode != FT_MODE_FOE) ||
@@ -301,6 +302,7 @@ extern "C" ft_status ttc_server_stream_bytes(const ttc_server *s, int H, int W, 
 
 extern "C" ft_status ttc_server_admit(ttc_server *s, int H, int W, int *stream_id)
 {
+    FT_API_RANGE;
     if (!s || !stream_id) return FT_ERR_INVALID_ARG;
     if (H > s->max_H || W > s->max_W) return FT_ERR_WORKSPACE;
     int64_t need = 0;
@@ -355,6 +357,7 @@ extern "C" ft_status ttc_server_submit(ttc_server *s, int id, const void *frame,
 
 extern "C" ft_status ttc_server_step(ttc_server *s, int wait, ttc_served *done, int max_done, int *n_done)
 {
+    FT_API_RANGE;
     if (!s || !n_done || (max_done > 0 && !done) || max_done < 0) return FT_ERR_INVALID_ARG;
     *n_done = 0;
     ft_status st = collect(s, false);
@@ -395,6 +398,7 @@ extern "C" ft_status ttc_server_drive(ttc_server *s, const int *ids, int nstream
                                       const int64_t *pitches, int nframes, int64_t pairs, double *seconds,
                                       int64_t *served, double *p50_ms, double *p99_ms)
 {
+    FT_API_RANGE;
     if (!s || !ids || !frames || !pitches || nstreams < 1 || nframes < 1 || pairs < 1) return FT_ERR_INVALID_ARG;
     for (int i = 0; i < nstreams; ++i)
         if (ids[i] < 0 || ids[i] >= (int)s->streams.size() || !s->streams[(size_t)ids[i]].open)

@@ -16,7 +16,6 @@
 
 #include "common.cuh"
 #include "ttc_pass.cuh"
-#include "ttc_levels.cuh"
 #include "ttc_merge.cuh"
 #include "ttc_tma.cuh"
 
@@ -294,7 +293,6 @@ struct ttc_ctx {
     float *partials;
     unsigned char *images;
     int *status;              // stage-1 timeout flag
-    int *counters;            // 64 bytes after status: the levels kernel's ticket [0] and tile counts [32...]
     int64_t partial_cap;      // floats
     int64_t image_cap;        // bytes
     size_t bytes;
@@ -309,9 +307,7 @@ struct ttc_ctx {
     CUtensorMap *d_maps;              // [max_pairs][4]: level-0 maps of pairs the TMA kernel takes
     int2 *d_items;                    // [items_cap]: (pair, tile) of the TMA kernel's level-0 items
     size_t items_cap;
-    int2 *d_items1;                   // [items1_cap]: (pair, tile) of the levels kernel's items
-    size_t items1_cap;
-    size_t off_maps, off_items, off_items1;   // byte offsets of those arrays in the staging buffers
+    size_t off_maps, off_items;       // byte offsets of those arrays in the staging buffers
     unsigned char *h_stage;           // pinned staging buffer of the arrays
     size_t stage_bytes;
     cudaEvent_t stage_ev;             // the last upload from h_stage
@@ -321,8 +317,6 @@ struct ttc_ctx {
         int rpw[FT_MAX_LEVELS], in_es[FT_MAX_LEVELS], out_es[FT_MAX_LEVELS];
         int n_int[FT_MAX_LEVELS], n_edge[FT_MAX_LEVELS];
         int n_tma;                    // level-0 items of the TMA kernel (uint8 pairs it can read)
-        int lbegin[FT_MAX_LEVELS + 1];  // levels kernel: first item of level l (l >= 1)
-        bool fused;                   // levels >= 1 and the solve run in the levels kernel
         bool ready;
     } b;
     int plan_rpw[FT_MAX_LEVELS];      // tile rows per warp per level for batches (0: automatic)
@@ -342,6 +336,7 @@ struct ttc_ctx {
 
 extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max_levels, int max_pairs)
 {
+    FT_API_RANGE;
     if (!ctx) return FT_ERR_INVALID_ARG;
     *ctx = nullptr;
     if (max_pairs < 1 || max_levels < 1) return FT_ERR_INVALID_ARG;
@@ -359,8 +354,8 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     const int64_t ib = std::max(g.image_bytes, g16.image_bytes);
     float *part = nullptr;
     unsigned char *img = nullptr;
-    // the partials, then the status word and (64 bytes on) the levels kernel's counters
-    const size_t cbytes = ((64 + (32 + (size_t)max_levels * max_pairs) * sizeof(int)) + 255) / 256 * 256;
+    // the partials, then 256 bytes holding the status word
+    const size_t cbytes = 256;
     cudaError_t e = cudaMalloc(&part, (size_t)pf * sizeof(float) + cbytes);
     if (e == cudaSuccess && ib > 0) e = cudaMalloc(&img, (size_t)ib);
     if (e != cudaSuccess) {
@@ -381,7 +376,6 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->partials = part;
     c->images = img;
     c->status = reinterpret_cast<int *>(part + pf);
-    c->counters = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(c->status) + 64);
     c->partial_cap = pf;
     c->image_cap = ib;
     c->bytes = (size_t)pf * sizeof(float) + cbytes + (size_t)ib;
@@ -396,13 +390,7 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->items_cap = tiles0 * (size_t)max_pairs;
     c->off_maps = (b_desc + b_pre + b_sd + 127) / 128 * 128;
     c->off_items = c->off_maps + (size_t)max_pairs * 4 * sizeof(CUtensorMap);
-    // levels >= 1 of every pair, at the smaller tile height (the most tiles)
-    size_t tiles1 = 0;
-    for (int l = 1; l < max_levels && (max_H >> l) >= 2 && (max_W >> l) >= 2; ++l)
-        tiles1 += (size_t)ft::ceil_div((max_H >> l) - 1, ttc_pass::TR_SMALL) * (size_t)ft::ceil_div((max_W >> l) - 1, TC);
-    c->items1_cap = tiles1 * (size_t)max_pairs;
-    c->off_items1 = c->off_items + c->items_cap * sizeof(int2);
-    c->stage_bytes = c->off_items1 + c->items1_cap * sizeof(int2);
+    c->stage_bytes = c->off_items + c->items_cap * sizeof(int2);
     unsigned char *dbuf = nullptr;
     e = cudaMalloc(&dbuf, c->stage_bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(&c->h_stage, c->stage_bytes, cudaHostAllocDefault);
@@ -434,7 +422,6 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->d_sdesc = reinterpret_cast<SolveDesc *>(dbuf + b_desc + b_pre);
     c->d_maps = reinterpret_cast<CUtensorMap *>(dbuf + c->off_maps);
     c->d_items = reinterpret_cast<int2 *>(dbuf + c->off_items);
-    c->d_items1 = reinterpret_cast<int2 *>(dbuf + c->off_items1);
     c->bytes += c->stage_bytes;
     *ctx = c;
     if (!c->ring_ready) {
@@ -569,59 +556,12 @@ cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs
 // independent = 0 for the consecutive pairs of a video (frame t+1 shared)
 // the levels kernel takes levels 1 .. L-1 in one launch when their images have one pixel
 // type: uint16 (uint8 frames, at most 5 levels) or float (float frames)
-// Levels >= 1: one launch per level (tile sets of ttc_pass_kernel / ttc_batch_kernel)
-// and a merge/solve launch by default; 1: the persistent levels kernel
-// (ttc_levels.cuh), which measured slower on GB300 (1080p video, 299 pairs: 1.32 against
-// 1.09 ms per step; 512 uneven pairs: 1.27 against 1.11 ms per batch).
-#ifndef FT_FUSE_LEVELS
-#define FT_FUSE_LEVELS 0
-#endif
-
-bool levels_kernel_fits(int dtype, int levels)
-{
-    return FT_FUSE_LEVELS && levels >= 2 && (dtype == FT_F32 || levels <= 5);
-}
-
-// merge + solve requested from launch_partials (fused into the levels kernel)
-struct SolveReq {
-    int mode;
-    ttc_level_result *out;
-    int skip;                         // pairs [0, skip) are not written
-};
-
-int sm_count()
-{
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    return std::max(nsm, 1);
-}
-
-template <typename Tin, bool VIDEO>
-cudaError_t launch_levels_t(const ttc_levels::LevelsParams &lp, cudaStream_t s)
-{
-    const int total = lp.begin[lp.levels];
-    if (total <= 0) return cudaSuccess;
-    const int grid = std::min(total, FT_TTC_MINB * sm_count());
-    ttc_levels::ttc_levels_kernel<Tin, VIDEO><<<grid, ttc_pass::NT, 0, s>>>(lp);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_levels(const ttc_levels::LevelsParams &lp, int dtype, bool video, cudaStream_t s)
-{
-    if (dtype == FT_U8)
-        return video ? launch_levels_t<unsigned short, true>(lp, s) : launch_levels_t<unsigned short, false>(lp, s);
-    return video ? launch_levels_t<float, true>(lp, s) : launch_levels_t<float, false>(lp, s);
-}
-
 // all levels of npairs pairs: pair p is (prev + p * pair_stride, cur + p * pair_stride);
-// independent = 0 for the consecutive pairs of a video (frame t+1 shared).  With `req`,
-// the merge + solve runs inside the levels kernel when that kernel is used (*solved).
+// independent = 0 for the consecutive pairs of a video (frame t+1 shared)
 ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64_t pair_stride, int npairs,
                           int independent, int dtype, int H, int W, int64_t pitch, int levels, cudaStream_t s,
-                          int plan_pairs = 0, const SolveReq *req = nullptr, bool *solved = nullptr)
+                          int plan_pairs = 0)
 {
-    if (solved) *solved = false;
     if (!ctx || !prev || !cur) return FT_ERR_INVALID_ARG;
     if (npairs < 1) return FT_ERR_SHAPE;
     ft_status st = check_frames(dtype, H, W, pitch);
@@ -649,12 +589,15 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
             p.cur = static_cast<const unsigned char *>(cur);
             p.pair_stride = pair_stride;
             p.pitch = pitch;
+            p.frame_bytes = pitch * (H - 1) + (int64_t)W * g.esize[0];
         } else {
             p.prev = ctx->images + g.ioff[l];
             p.cur = p.prev + g.fstride[l];
             p.pair_stride = independent ? 2 * g.fstride[l] : g.fstride[l];
             p.pitch = g.pitch[l];
+            p.frame_bytes = g.fstride[l];
         }
+        p.status = ctx->status;
         p.H = g.H[l];
         p.W = g.W[l];
         p.tiles_x = g.tiles_x[l];
@@ -672,22 +615,20 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
             p.next = ctx->images + g.ioff[l + 1];
             p.next_fstride = g.fstride[l + 1];
             p.next_pitch = g.pitch[l + 1];
+            p.next_bytes = g.fstride[l + 1];
             out_es[l] = g.esize[l + 1];
         }
         p.write_prev = independent;
         p.vec = l == 0 ? vec0 : 1;
         p.padded = l == 0 ? 0 : 1;
     }
-    const bool fused = levels_kernel_fits(dtype, levels);
-    // the status word and, after it, the levels kernel's ticket and tile counters
-    const size_t zero_bytes = fused ? 64 + (32 + (size_t)levels * npairs) * sizeof(int) : sizeof(int);
-    cudaError_t e = cudaMemsetAsync(ctx->status, 0, zero_bytes, s);
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
     if (e == cudaSuccess && ctx->ev0_start) e = cudaEventRecord(ctx->ev0_start, s);
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
         return FT_ERR_CUDA;
     }
-    for (int l = 0; l < (fused ? 1 : levels); ++l) {
+    for (int l = 0; l < levels; ++l) {
         const ttc_pass::PassParams &p = pp[l];
         const int in_es = g.esize[l];
         bool done = false;
@@ -707,42 +648,6 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
             ft::set_cuda_error(e);
             return FT_ERR_CUDA;
         }
-    }
-    if (fused) {
-        ttc_levels::LevelsParams lp{};
-        lp.levels = levels;
-        lp.npairs = npairs;
-        lp.begin[1] = 0;
-        for (int l = 1; l < levels; ++l) {
-            lp.lvl[l] = pp[l];
-            lp.ntiles[l] = g.ntiles[l];
-            lp.rpw[l] = g.tr[l] / 8;
-            lp.begin[l + 1] = lp.begin[l] + npairs * g.ntiles[l];
-        }
-        for (int l = 0; l < levels; ++l) lp.ntiles[l] = g.ntiles[l];
-        lp.tickets = ctx->counters;
-        lp.done = ctx->counters + 32;
-        lp.status = ctx->status;
-        if (req) {
-            lp.solve = 1;
-            lp.mode = req->mode;
-            lp.skip = req->skip;
-            lp.out = req->out;
-            lp.partials = ctx->partials;
-            for (int l = 0; l < levels; ++l) {
-                lp.poff[l] = g.poff[l];
-                lp.inv_scale[l] = std::ldexp(1.0, -4 - 4 * l - g.shift[l]);
-                lp.ncubes[l] = (int64_t)(g.H[l] - 1) * (int64_t)(g.W[l] - 1);
-            }
-        }
-        if ((int64_t)lp.begin[levels] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
-        e = launch_levels(lp, dtype, true, s);
-        if (e != cudaSuccess) {
-            ft::set_cuda_error(e);
-            return FT_ERR_CUDA;
-        }
-        ++launches;
-        if (req && solved) *solved = true;
     }
     ctx->g = g;
     ctx->ready = true;
@@ -779,6 +684,7 @@ ft_status launch_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream
 extern "C" ft_status ttc_partial_sums(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
                                       int dtype, int H, int W, int64_t pitch_bytes, int levels, void *stream)
 {
+    FT_API_RANGE;
     if (!ctx || !frames) return FT_ERR_INVALID_ARG;
     if (T < 2) return FT_ERR_SHAPE;
     if (frame_stride_bytes < 0) return FT_ERR_INVALID_ARG;
@@ -789,6 +695,7 @@ extern "C" ft_status ttc_partial_sums(ttc_ctx *ctx, const void *frames, int64_t 
 
 extern "C" ft_status ttc_reduce_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, void *stream)
 {
+    FT_API_RANGE;
     return launch_solve(ctx, mode, out, ft::as_stream(stream));
 }
 
@@ -808,13 +715,12 @@ extern "C" ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, 
                                int64_t pitch_bytes, int levels, int mode, ttc_level_result *out,
                                void *stream)
 {
+    FT_API_RANGE;
     if (!ctx || !prev || !cur || !out) return FT_ERR_INVALID_ARG;
     if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
-    const SolveReq req{mode, out, 0};
-    bool solved = false;
     ft_status st = launch_partials(ctx, prev, cur, 0, 1, 0, dtype, H, W, pitch_bytes, levels,
-                                   ft::as_stream(stream), 0, &req, &solved);
-    if (st != FT_OK || solved) return st;
+                                   ft::as_stream(stream));
+    if (st != FT_OK) return st;
     return solve_after(ctx, mode, out, ft::as_stream(stream));
 }
 
@@ -930,13 +836,16 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
                 q.cur = static_cast<const unsigned char *>(d.cur);
                 q.pitch = d.pitch_bytes;
                 q.vec = vec0;
+                q.frame_bytes = d.pitch_bytes * (d.H - 1) + (int64_t)d.W * es0;
             } else {
                 q.prev = prev_off[l] >= 0 ? ctx->images + prev_off[l]
                                           : static_cast<const unsigned char *>(d.prev_pyramid) + pyr_off[l];
                 q.cur = cur_img(l);
                 q.pitch = img_pitch[l];
                 q.vec = 1;
+                q.frame_bytes = img_fs[l];
             }
+            q.status = ctx->status;
             q.set = q.vec ? ttc_pass::SET_EDGES : ttc_pass::SET_ALL;
             const double pl = (double)(1 << l);
             q.xoff = (float)(0.5 - ((double)d.W - pl) / (2.0 * pl));
@@ -947,6 +856,7 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
                 q.next = prev_img(l + 1);
                 q.next_cur = cur_img(l + 1);
                 q.next_pitch = img_pitch[l + 1];
+                q.next_bytes = img_fs[l + 1];
             }
             hd[(size_t)l * ctx->max_pairs + p] = q;
             const bool by_tma = l == 0 && tma;
@@ -981,23 +891,6 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
     for (int l = 0; l < levels; ++l)
         if (n_int[l] > 0x7fffffffLL || n_edge[l] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
     if (n_tma > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
-    // levels >= 1 in the levels kernel: items level-major, pair-major within a level
-    const bool fused = levels_kernel_fits(dtype, levels);
-    int2 *hitems1 = reinterpret_cast<int2 *>(ctx->h_stage + ctx->off_items1);
-    int64_t n1 = 0;
-    int lbegin[FT_MAX_LEVELS + 1] = {0};
-    if (fused) {
-        for (int l = 1; l < levels; ++l) {
-            lbegin[l] = (int)n1;
-            for (int p = 0; p < npairs; ++p) {
-                const int nt = hd[(size_t)l * ctx->max_pairs + p].ntiles;
-                if (n1 + nt > (int64_t)ctx->items1_cap || n1 + nt > 0x7fffffffLL) return FT_ERR_WORKSPACE;
-                for (int t = 0; t < nt; ++t) hitems1[n1 + t] = make_int2(p, t);
-                n1 += nt;
-            }
-        }
-        lbegin[levels] = (int)n1;
-    }
     unsigned char *dstage = reinterpret_cast<unsigned char *>(ctx->d_descs);
     cudaError_t e = cudaMemcpyAsync(dstage, ctx->h_stage, ctx->off_maps, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n_tma > 0)
@@ -1006,17 +899,12 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
     if (e == cudaSuccess && n_tma > 0)
         e = cudaMemcpyAsync(dstage + ctx->off_items, ctx->h_stage + ctx->off_items, (size_t)n_tma * sizeof(int2),
                             cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n1 > 0)
-        e = cudaMemcpyAsync(dstage + ctx->off_items1, ctx->h_stage + ctx->off_items1, (size_t)n1 * sizeof(int2),
-                            cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev, s);
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
         return FT_ERR_CUDA;
     }
     ctx->stage_pending = true;
-    ctx->b.fused = fused;
-    for (int l = 0; l <= levels; ++l) ctx->b.lbegin[l] = lbegin[l];
     if (pairs != ctx->h_pairs)
         for (int p = 0; p < npairs; ++p) ctx->h_pairs[p] = pairs[p];
     ctx->b.npairs = npairs;
@@ -1057,10 +945,8 @@ ft_status batch_run_impl(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStre
     if (!ctx->b.ready) return FT_ERR_INVALID_ARG;
     const auto &b = ctx->b;
     int count = 0;
-    // the status word and, after it, the levels kernel's ticket and tile counters
-    const size_t zero_bytes = b.fused ? 64 + (32 + (size_t)b.levels * b.npairs) * sizeof(int) : sizeof(int);
-    cudaError_t e = cudaMemsetAsync(ctx->status, 0, zero_bytes, s);
-    for (int l = 0; l < (b.fused ? 1 : b.levels) && e == cudaSuccess; ++l) {
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
+    for (int l = 0; l < b.levels && e == cudaSuccess; ++l) {
         if (l == 0 && b.n_tma > 0) {
             ttc_tma::BatchItems it{ctx->d_descs, ctx->d_maps, ctx->d_items, b.n_tma};
             e = launch_tma_items(it, b.levels > 1, ctx->status, s);
@@ -1071,33 +957,11 @@ ft_status batch_run_impl(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStre
         else if (b.in_es[l] == 2) e = batch_level<unsigned short>(ctx, l, &count, s);
         else e = batch_level<float>(ctx, l, &count, s);
     }
-    if (e == cudaSuccess && b.fused) {
-        // levels 1 .. L-1 and the merge + solve of every pair in one launch
-        ttc_levels::LevelsParams lp{};
-        lp.descs = ctx->d_descs;
-        lp.desc_stride = ctx->max_pairs;
-        lp.items = ctx->d_items1;
-        lp.levels = b.levels;
-        lp.npairs = b.npairs;
-        for (int l = 0; l <= b.levels; ++l) lp.begin[l] = b.lbegin[l];
-        for (int l = 1; l < b.levels; ++l) lp.rpw[l] = b.rpw[l];
-        lp.tickets = ctx->counters;
-        lp.done = ctx->counters + 32;
-        lp.status = ctx->status;
-        lp.solve = 1;
-        lp.mode = mode;
-        lp.partials = ctx->partials;
-        lp.sdesc = ctx->d_sdesc;
-        lp.out = out;
-        if (e == cudaSuccess) e = launch_levels(lp, b.dtype, false, s);
+    if (e == cudaSuccess) {
+        ttc_batch_solve_kernel<<<(unsigned)(b.npairs * b.levels), 32, 0, s>>>(ctx->partials, ctx->d_sdesc, mode,
+                                                                              ctx->status, out);
+        e = cudaGetLastError();
         ++count;
-    } else {
-        if (e == cudaSuccess) {
-            ttc_batch_solve_kernel<<<(unsigned)(b.npairs * b.levels), 32, 0, s>>>(ctx->partials, ctx->d_sdesc, mode,
-                                                                                  ctx->status, out);
-            e = cudaGetLastError();
-            ++count;
-        }
     }
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
@@ -1112,17 +976,20 @@ ft_status batch_run_impl(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStre
 extern "C" ft_status ttc_batch_prepare(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npairs, int dtype, int levels,
                                        void *stream)
 {
+    FT_API_RANGE;
     return batch_prepare_impl(ctx, pairs, npairs, dtype, levels, ft::as_stream(stream));
 }
 
 extern "C" ft_status ttc_batch_run(ttc_ctx *ctx, int mode, ttc_level_result *out, void *stream)
 {
+    FT_API_RANGE;
     return batch_run_impl(ctx, mode, out, ft::as_stream(stream));
 }
 
 extern "C" ft_status ttc_batch_autotune(ttc_ctx *ctx, int mode, ttc_level_result *out, int reps, int *rows_per_tile,
                                         void *stream)
 {
+    FT_API_RANGE;
     if (!ctx || !out || reps < 1) return FT_ERR_INVALID_ARG;
     if (!ctx->b.ready) return FT_ERR_INVALID_ARG;
     cudaStream_t s = ft::as_stream(stream);
@@ -1286,8 +1153,7 @@ extern "C" ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dt
     if ((st = check_levels(H, W, levels)) != FT_OK) return st;
     Geometry g;
     geometry(H, W, levels, dtype, 1, 2, g);
-    // layout: 256 bytes for the status word and the levels kernel's counters, the
-    // partials, the level images
+    // layout: 256 bytes for the status word, the partials, the level images
     const int64_t pbytes = 256 + (g.partial_floats * (int64_t)sizeof(float) + 255) / 256 * 256;
     if (pbytes + g.image_bytes > (int64_t)FT_NOALLOC_SCRATCH_BYTES) return FT_ERR_WORKSPACE;
     unsigned char *base = nullptr;
@@ -1299,18 +1165,14 @@ extern "C" ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dt
     c.max_levels = levels;
     c.max_pairs = 1;
     c.status = reinterpret_cast<int *>(base);
-    c.counters = reinterpret_cast<int *>(base + 64);    // ticket, then (32 ints on) one count per level
     c.partials = reinterpret_cast<float *>(base + 256);
     c.images = base + pbytes;
     c.partial_cap = g.partial_floats;
     c.image_cap = g.image_bytes;
     c.bytes = FT_NOALLOC_SCRATCH_BYTES;
     c.ready = false;
-    const SolveReq req{mode, out, 0};
-    bool solved = false;
-    st = launch_partials(&c, prev, cur, 0, 1, 0, dtype, H, W, pitch_bytes, levels, ft::as_stream(stream), 0, &req,
-                         &solved);
-    if (st != FT_OK || solved) return st;
+    st = launch_partials(&c, prev, cur, 0, 1, 0, dtype, H, W, pitch_bytes, levels, ft::as_stream(stream));
+    if (st != FT_OK) return st;
     return launch_solve(&c, mode, out, ft::as_stream(stream));
 }
 
@@ -1318,16 +1180,15 @@ extern "C" ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_
                                         int dtype, int H, int W, int64_t pitch_bytes, int levels, int mode,
                                         ttc_level_result *out, void *stream)
 {
+    FT_API_RANGE;
     if (!ctx || !frames || !out) return FT_ERR_INVALID_ARG;
     if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
     if (T < 2) return FT_ERR_SHAPE;
     if (frame_stride_bytes < 0) return FT_ERR_INVALID_ARG;
     const unsigned char *f0 = static_cast<const unsigned char *>(frames);
-    const SolveReq req{mode, out, 0};
-    bool solved = false;
     ft_status st = launch_partials(ctx, f0, f0 + frame_stride_bytes, frame_stride_bytes, T - 1, 0, dtype, H, W,
-                                   pitch_bytes, levels, ft::as_stream(stream), 0, &req, &solved);
-    if (st != FT_OK || solved) return st;
+                                   pitch_bytes, levels, ft::as_stream(stream));
+    if (st != FT_OK) return st;
     return solve_after(ctx, mode, out, ft::as_stream(stream));
 }
 
@@ -1369,6 +1230,7 @@ ft_status host_plan(const ttc_ctx *ctx, int64_t frame_stride_bytes, int T, int d
 extern "C" ft_status ttc_ctx_reserve_host(ttc_ctx *ctx, int64_t frame_stride_bytes, int T, int dtype, int H, int W,
                                           int64_t pitch_bytes, int levels)
 {
+    FT_API_RANGE;
     if (!ctx) return FT_ERR_INVALID_ARG;
     if (!ctx->ring_ready) return FT_ERR_CUDA;
     HostPlan hp;
@@ -1417,6 +1279,7 @@ extern "C" ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, i
                                              int dtype, int H, int W, int64_t pitch_bytes, int levels, int mode,
                                              ttc_level_result *out, void *stream)
 {
+    FT_API_RANGE;
     if (!ctx || !frames || !out) return FT_ERR_INVALID_ARG;
     if (mode != FT_MODE_TTC && mode != FT_MODE_FOE) return FT_ERR_INVALID_ARG;
     if (!ctx->ring_ready) return FT_ERR_CUDA;
@@ -1450,15 +1313,14 @@ extern "C" ft_status ttc_solve_sequence_host(ttc_ctx *ctx, const void *frames, i
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied[b], cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_copied[b], 0);
         if (e != cudaSuccess) break;
-        const SolveReq req{mode, ctx->ring_out + (size_t)f0 * levels, x};
-        bool solved = false;
         st = launch_partials(ctx, dev, dev + frame_stride_bytes, frame_stride_bytes, n + x, 0, dtype, H, W,
-                             pitch_bytes, levels, s, npairs, &req, &solved);
+                             pitch_bytes, levels, s, npairs);
         if (st != FT_OK) return st;
-        launches += ctx->launches + (solved ? 0 : 1);
+        launches += ctx->launches + 1;
         e = cudaEventRecord(ctx->ev_free[b], s);
         if (e != cudaSuccess) break;
-        if (!solved && (st = launch_solve(ctx, mode, req.out, s, x)) != FT_OK) return st;
+        st = launch_solve(ctx, mode, ctx->ring_out + (size_t)f0 * levels, s, x);
+        if (st != FT_OK) return st;
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, ctx->ring_out, (size_t)npairs * levels * sizeof(ttc_level_result),
@@ -1477,6 +1339,7 @@ extern "C" ft_status ttc_derivatives(const void *prev, const void *cur, int dtyp
                                      int64_t pitch_bytes, float *Ex, float *Ey, float *Et, float *G,
                                      void *stream)
 {
+    FT_API_RANGE;
     if (!prev || !cur || !Ex || !Ey || !Et) return FT_ERR_INVALID_ARG;
     ft_status st = check_frames(dtype, H, W, pitch_bytes);
     if (st != FT_OK) return st;
@@ -1499,6 +1362,7 @@ extern "C" ft_status ttc_derivatives(const void *prev, const void *cur, int dtyp
 extern "C" ft_status ttc_gradient_batch(const void *images, int n, int64_t image_stride_bytes, int dtype, int H,
                                         int W, int64_t pitch_bytes, float *mag, float *dir, void *stream)
 {
+    FT_API_RANGE;
     if (!images || (!mag && !dir)) return FT_ERR_INVALID_ARG;
     const ft_status st = check_frames(dtype, H, W, pitch_bytes);
     if (st != FT_OK) return st;

@@ -1,6 +1,6 @@
 // Stage 2 of the TTC/FOE solve (Sec. V-A, Eq. final_TTC): the FP64 merge of a
 // (pair, level)'s tile partials in a fixed order and the solve of the normal
-// equations, shared by the merge kernels and the levels kernel.
+// equations, shared by the merge kernels.
 #pragma once
 
 #include "common.cuh"
@@ -90,10 +90,8 @@ __device__ void solve_one(const double s[NSUM], int mode, int level, ttc_level_r
 
 // One warp: FP64 merge of ntiles FP32 tile partials in a fixed order (lane-strided,
 // then a shuffle tree), scaling to level-l mean-image units, solve; lane 0 writes.
-// CG: the partials were written by other CTAs of the same launch (read from L2).
-template <bool CG>
-__device__ __forceinline__ void merge_solve_t(const float *src, int ntiles, int l, double inv_scale, int64_t ncubes,
-                                              int mode, const int *status, ttc_level_result *out)
+__device__ __forceinline__ void merge_solve(const float *src, int ntiles, int l, double inv_scale, int64_t ncubes,
+                                            int mode, const int *status, ttc_level_result *out)
 {
     const int lane = threadIdx.x & 31;
     double acc[NSUM];
@@ -101,7 +99,7 @@ __device__ __forceinline__ void merge_solve_t(const float *src, int ntiles, int 
     for (int s = 0; s < NSUM; ++s) acc[s] = 0.0;
     for (int t = lane; t < ntiles; t += 32)
 #pragma unroll
-        for (int s = 0; s < NSUM; ++s) acc[s] += (double)(CG ? __ldcg(src + t * NSUM + s) : src[t * NSUM + s]);
+        for (int s = 0; s < NSUM; ++s) acc[s] += (double)src[t * NSUM + s];
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1)
 #pragma unroll
@@ -111,21 +109,12 @@ __device__ __forceinline__ void merge_solve_t(const float *src, int ntiles, int 
         for (int s = 0; s < NSUM; ++s) r.sums[s] = acc[s] * inv_scale;
         r.n = ncubes;
         solve_one(r.sums, mode, l, &r);
-        if (*reinterpret_cast<const volatile int *>(status)) r.flags |= FT_FLAG_TIMEOUT;
+        // status word: bit 0 a wait gave up, bit 1 a checked build found an access out of bounds
+        const int st = *status;
+        if (st & 1) r.flags |= FT_FLAG_TIMEOUT;
+        if (st & 2) r.flags |= FT_FLAG_BOUNDS;
         *out = r;
     }
-}
-
-__device__ __forceinline__ void merge_solve(const float *src, int ntiles, int l, double inv_scale, int64_t ncubes,
-                                            int mode, const int *status, ttc_level_result *out)
-{
-    merge_solve_t<false>(src, ntiles, l, inv_scale, ncubes, mode, status, out);
-}
-
-__device__ __forceinline__ void merge_solve_cg(const float *src, int ntiles, int l, double inv_scale,
-                                               int64_t ncubes, int mode, const int *status, ttc_level_result *out)
-{
-    merge_solve_t<true>(src, ntiles, l, inv_scale, ncubes, mode, status, out);
 }
 
 }  // namespace ttc_merge

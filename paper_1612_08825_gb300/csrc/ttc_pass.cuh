@@ -58,7 +58,27 @@ struct PassParams {
                                 // -1: the first frame's level l+1 exists already (not written)
     unsigned char *next_cur;    // non-null: level-(l+1) image of the second frame (one pair per launch
                                 // item); null: the frame after the first one in `next`
+    int64_t frame_bytes;        // bytes readable from a frame's first pixel (checked builds)
+    int64_t next_bytes;         // bytes writable from a next-level image's first pixel (checked builds)
+    int *status;                // the call's status word (checked builds: bit 1 on an access out of bounds)
 };
+
+// Checked builds (FASTTTC_CHECK=1 at build time defines FT_CHECK): every global read of a
+// frame and every store of a next-level pixel is compared with the extent the call gave;
+// one outside it sets bit 1 of the status word (FT_FLAG_BOUNDS in the records) and is
+// skipped (reads give zero).  Release builds compile the checks away.
+#ifndef FT_CHECK
+#define FT_CHECK 0
+#endif
+
+__device__ __forceinline__ bool in_extent(const PassParams &p, const void *base, const void *addr, int bytes,
+                                          int64_t extent)
+{
+    const int64_t off = reinterpret_cast<const unsigned char *>(addr) - reinterpret_cast<const unsigned char *>(base);
+    if (off >= 0 && off + bytes <= extent) return true;
+    if (p.status) atomicOr(p.status, 2);
+    return false;
+}
 
 // ---------------------------------------------------------------------------
 // packed FP32 pairs
@@ -158,21 +178,6 @@ template <> struct Pix<float> {
     __device__ static float ld1(const float *p) { return __ldg(p); }
 };
 
-// Loads of pixel data: through the read-only path (__ldg), or, for images another CTA
-// of the same launch may have written (CG), from L2 (__ldcg, coherent at the device
-// level once the writer's release has been observed).
-template <bool CG, typename V>
-__device__ __forceinline__ V ldx(const V *p)
-{
-    return CG ? __ldcg(p) : __ldg(p);
-}
-
-template <bool CG, typename T>
-__device__ __forceinline__ typename Pix<T>::Vec vld4(const T *p)
-{
-    return ldx<CG>(reinterpret_cast<const typename Pix<T>::Vec *>(p));
-}
-
 // raw loads of one row of both frames: 4 columns in each half + the column right of
 // the right half (used by lane 31 only); zero outside the image
 template <typename T> struct RawRow {
@@ -182,47 +187,44 @@ template <typename T> struct RawRow {
 
 // element loads with bounds checks; whole groups inside the row use one vector load
 // (vec: the rows allow it)
-template <bool CG>
 __device__ __forceinline__ uint32_t load4_checked(const unsigned char *row, int col, int W, bool rowok, int vec)
 {
-    if (vec && rowok && col + 4 <= W) return ldx<CG>(reinterpret_cast<const unsigned int *>(row + col));
+    if (vec && rowok && col + 4 <= W) return __ldg(reinterpret_cast<const unsigned int *>(row + col));
     uint32_t w = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool ok = rowok && col + k < W;
-        const uint32_t v = ldx<CG>(row + (ok ? col + k : 0));
+        const uint32_t v = __ldg(row + (ok ? col + k : 0));
         w |= (ok ? v : 0u) << (8 * k);
     }
     return w;
 }
-template <bool CG>
 __device__ __forceinline__ uint2 load4_checked(const unsigned short *row, int col, int W, bool rowok, int vec)
 {
-    if (vec && rowok && col + 4 <= W) return ldx<CG>(reinterpret_cast<const uint2 *>(row + col));
+    if (vec && rowok && col + 4 <= W) return __ldg(reinterpret_cast<const uint2 *>(row + col));
     uint32_t v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool ok = rowok && col + k < W;
-        const uint32_t x = ldx<CG>(row + (ok ? col + k : 0));
+        const uint32_t x = __ldg(row + (ok ? col + k : 0));
         v[k] = ok ? x : 0u;
     }
     return make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
 }
-template <bool CG>
 __device__ __forceinline__ float4 load4_checked(const float *row, int col, int W, bool rowok, int vec)
 {
-    if (vec && rowok && col + 4 <= W) return ldx<CG>(reinterpret_cast<const float4 *>(row + col));
+    if (vec && rowok && col + 4 <= W) return __ldg(reinterpret_cast<const float4 *>(row + col));
     float v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool ok = rowok && col + k < W;
-        const float x = ldx<CG>(row + (ok ? col + k : 0));
+        const float x = __ldg(row + (ok ? col + k : 0));
         v[k] = ok ? x : 0.f;
     }
     return make_float4(v[0], v[1], v[2], v[3]);
 }
 
-template <typename T, bool ROWCHK, bool COLCHK, bool VEC, bool CG = false>
+template <typename T, bool ROWCHK, bool COLCHK, bool VEC>
 __device__ __forceinline__ void load_raw(const PassParams &p, const T *fa, const T *fb, int gy, int gcl, RawRow<T> &r)
 {
     const bool rowok = !ROWCHK || gy < p.H;
@@ -233,22 +235,48 @@ __device__ __forceinline__ void load_raw(const PassParams &p, const T *fa, const
     const int gcr = gcl + HALF;
     if (!COLCHK && VEC) {
         const typename Pix<T>::Vec z = Pix<T>::zero();
-        const typename Pix<T>::Vec al = vld4<CG>(ra + gcl), ar = vld4<CG>(ra + gcr);
-        const typename Pix<T>::Vec bl = vld4<CG>(rb + gcl), br = vld4<CG>(rb + gcr);
+        if (FT_CHECK) {
+            constexpr int VB = 4 * (int)sizeof(T);
+            const bool ok = in_extent(p, fa, ra + gcl, VB, p.frame_bytes) &&
+                            in_extent(p, fa, ra + gcr, VB, p.frame_bytes) &&
+                            in_extent(p, fb, rb + gcl, VB, p.frame_bytes) &&
+                            in_extent(p, fb, rb + gcr, VB, p.frame_bytes);
+            if (!ok) {
+                r.al = r.ar = r.bl = r.br = z;
+                r.a4 = r.b4 = 0.f;
+                return;
+            }
+        }
+        const typename Pix<T>::Vec al = Pix<T>::ld4(ra + gcl), ar = Pix<T>::ld4(ra + gcr);
+        const typename Pix<T>::Vec bl = Pix<T>::ld4(rb + gcl), br = Pix<T>::ld4(rb + gcr);
         r.al = rowok ? al : z;
         r.ar = rowok ? ar : z;
         r.bl = rowok ? bl : z;
         r.br = rowok ? br : z;
     } else {
-        r.al = load4_checked<CG>(ra, gcl, p.W, rowok, p.vec);
-        r.ar = load4_checked<CG>(ra, gcr, p.W, rowok, p.vec);
-        r.bl = load4_checked<CG>(rb, gcl, p.W, rowok, p.vec);
-        r.br = load4_checked<CG>(rb, gcr, p.W, rowok, p.vec);
+        // every element these loads may touch lies in the row's first W pixels
+        if (FT_CHECK && !(in_extent(p, fa, ra, (int)sizeof(T), p.frame_bytes) &&
+                          in_extent(p, fa, ra + (p.W - 1), (int)sizeof(T), p.frame_bytes) &&
+                          in_extent(p, fb, rb, (int)sizeof(T), p.frame_bytes) &&
+                          in_extent(p, fb, rb + (p.W - 1), (int)sizeof(T), p.frame_bytes))) {
+            r.al = r.ar = r.bl = r.br = Pix<T>::zero();
+            r.a4 = r.b4 = 0.f;
+            return;
+        }
+        r.al = load4_checked(ra, gcl, p.W, rowok, p.vec);
+        r.ar = load4_checked(ra, gcr, p.W, rowok, p.vec);
+        r.bl = load4_checked(rb, gcl, p.W, rowok, p.vec);
+        r.br = load4_checked(rb, gcr, p.W, rowok, p.vec);
     }
     const int c4 = gcr + 4;
     const bool ok4 = rowok && (!COLCHK || c4 < p.W);
     const int c4c = ok4 ? c4 : 0;
-    const float va = (float)ldx<CG>(ra + c4c), vb = (float)ldx<CG>(rb + c4c);
+    if (FT_CHECK && !(in_extent(p, fa, ra + c4c, (int)sizeof(T), p.frame_bytes) &&
+                      in_extent(p, fb, rb + c4c, (int)sizeof(T), p.frame_bytes))) {
+        r.a4 = r.b4 = 0.f;
+        return;
+    }
+    const float va = Pix<T>::ld1(ra + c4c), vb = Pix<T>::ld1(rb + c4c);
     r.a4 = ok4 ? va : 0.f;
     r.b4 = ok4 ? vb : 0.f;
 }
@@ -423,12 +451,14 @@ __device__ __forceinline__ void pyr_odd(const Pyr &py, const float2 A[4], const 
 // level-(l+1) pixels (row r1, columns c and c+1) of one frame from the thread's 2x2
 // block sums, written if they exist (r1 < H/2, column < W/2)
 template <typename Tout, bool EDGE>
-__device__ __forceinline__ void store_next(unsigned char *img, int64_t pitch, int r1, int c, float v0, float v1,
-                                           int Hn, int Wn)
+__device__ __forceinline__ void store_next(const PassParams &p, unsigned char *img, int64_t pitch, int r1, int c,
+                                           float v0, float v1, int Hn, int Wn)
 {
-    if (EDGE && r1 >= Hn) return;
+    if (EDGE && (r1 >= Hn || c >= Wn)) return;
+    const bool two = !EDGE || c + 1 < Wn;
     Tout *row = reinterpret_cast<Tout *>(img + (int64_t)r1 * pitch);
-    if (!EDGE || c + 1 < Wn) {
+    if (FT_CHECK && !in_extent(p, img, row + c, (two ? 2 : 1) * (int)sizeof(Tout), p.next_bytes)) return;
+    if (two) {
         if (sizeof(Tout) == 2) {
             // exact integers < 2^16: their bits are the low mantissa bits of 2^23 + v
             const uint32_t lo = __float_as_uint(v0 + 8388608.f) & 0xffffu;
@@ -437,14 +467,14 @@ __device__ __forceinline__ void store_next(unsigned char *img, int64_t pitch, in
         } else {
             *reinterpret_cast<float2 *>(row + c) = make_float2(v0, v1);
         }
-    } else if (c < Wn) {
+    } else {
         row[c] = sizeof(Tout) == 2 ? (Tout)(__float_as_uint(v0 + 8388608.f) & 0xffffu) : (Tout)v0;
     }
 }
 
 // R0, C0: first cube row / column the tile reads; cubes outside [ilo, ihi) x [jlo, jhi)
 // are masked (MASK only)
-template <typename Tin, typename Tout, bool ROWCHK, bool COLCHK, bool MASK, bool WRITE, int RPW, bool CG = false>
+template <typename Tin, typename Tout, bool ROWCHK, bool COLCHK, bool MASK, bool WRITE, int RPW>
 __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, const Tin *fb, int pair, int R0,
                                           int C0, int ilo, int ihi, int jlo, int jhi, float2 acc[NSUM])
 {
@@ -456,17 +486,15 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
     // consecutive pairs of a video share frames (frame t+1 of pair t is frame t+1 of
     // the next pair): the first frame is written by pair 0 only; independent pairs
     // own two frames each
-    // a descriptor with no next-level image (the last level) writes nothing, whatever WRITE
-    const bool wr = WRITE && (p.next != nullptr || p.next_cur != nullptr);
-    const bool wprev = wr && p.next != nullptr && (p.write_prev == 1 || (p.write_prev == 0 && pair == 0));
+    const bool wprev = WRITE && (p.write_prev == 1 || (p.write_prev == 0 && pair == 0));
     const int64_t fprev = p.write_prev == 1 ? 2 * (int64_t)pair : (int64_t)pair;
-    unsigned char *nprev = wprev ? p.next + fprev * p.next_fstride : nullptr;
-    unsigned char *ncur = wr ? (p.next_cur ? p.next_cur : p.next + (fprev + 1) * p.next_fstride) : nullptr;
+    unsigned char *nprev = WRITE && wprev ? p.next + fprev * p.next_fstride : nullptr;
+    unsigned char *ncur = WRITE ? (p.next_cur ? p.next_cur : p.next + (fprev + 1) * p.next_fstride) : nullptr;
 
     constexpr int PF = COLCHK ? 1 : (FT_TTC_PF < RPW ? FT_TTC_PF : RPW);
     RawRow<Tin> raw[RPW + 1];
 #pragma unroll
-    for (int r = 0; r < PF; ++r) load_raw<Tin, ROWCHK, COLCHK, !COLCHK, CG>(p, fa, fb, gr0 + r, gcl, raw[r]);
+    for (int r = 0; r < PF; ++r) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r, gcl, raw[r]);
 
     float2 xk[4];
 #pragma unroll
@@ -476,13 +504,13 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
     Pyr py;
 #pragma unroll
     for (int r = 0; r <= RPW; ++r) {
-        if (r + PF <= RPW) load_raw<Tin, ROWCHK, COLCHK, !COLCHK, CG>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
+        if (r + PF <= RPW) load_raw<Tin, ROWCHK, COLCHK, !COLCHK>(p, fa, fb, gr0 + r + PF, gcl, raw[r + PF]);
         float2 A[4], D[4];
         const int i = gr0 + r - 1;
         row_step<Tin, MASK>(raw[r], lane, st, r == 0, xk, y, i >= ilo && i < ihi, gcl, gcl + HALF, jlo, jhi, acc,
                             A, D);
         y = add2(y, make_float2(1.f, 1.f));
-        if (wr && r < RPW) {
+        if (WRITE && r < RPW) {
             if ((r & 1) == 0) {
                 pyr_even(py, A, D);
             } else {
@@ -490,11 +518,11 @@ __device__ __forceinline__ void pass_body(const PassParams &p, const Tin *fa, co
                 pyr_odd(py, A, D, va0, va1, vb0, vb1);
                 const int r1 = (gr0 >> 1) + (r >> 1);
                 const int cl = gcl >> 1, cr = (gcl + HALF) >> 1;
-                store_next<Tout, MASK>(ncur, p.next_pitch, r1, cl, vb0.x, vb1.x, Hn, Wn);
-                store_next<Tout, MASK>(ncur, p.next_pitch, r1, cr, vb0.y, vb1.y, Hn, Wn);
+                store_next<Tout, MASK>(p, ncur, p.next_pitch, r1, cl, vb0.x, vb1.x, Hn, Wn);
+                store_next<Tout, MASK>(p, ncur, p.next_pitch, r1, cr, vb0.y, vb1.y, Hn, Wn);
                 if (wprev) {
-                    store_next<Tout, MASK>(nprev, p.next_pitch, r1, cl, va0.x, va1.x, Hn, Wn);
-                    store_next<Tout, MASK>(nprev, p.next_pitch, r1, cr, va0.y, va1.y, Hn, Wn);
+                    store_next<Tout, MASK>(p, nprev, p.next_pitch, r1, cl, va0.x, va1.x, Hn, Wn);
+                    store_next<Tout, MASK>(p, nprev, p.next_pitch, r1, cr, va0.y, va1.y, Hn, Wn);
                 }
             }
         }

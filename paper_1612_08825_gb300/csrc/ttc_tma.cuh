@@ -32,7 +32,18 @@ constexpr int XBOX_PAD = (XBOX + 127) / 128 * 128;        // 1152 B
 constexpr int FRAME = 2 * BOX + XBOX_PAD;                 // 17792 B, 128-B multiple
 constexpr int BUF = 2 * FRAME;                            // both frames
 constexpr unsigned TX = 2u * (2u * BOX + XBOX);           // bytes the copies deliver per tile
-constexpr int SMEM = 2 * BUF + NSUM * NT * 4 + 2 * 8;     // two buffers, reduction, barriers
+
+// A batch tile's descriptor and origin, written to shared memory by the thread that
+// issues the tile's copies (before its arrive on the tile's barrier, whose completion
+// the consumers wait for), so that the CTA reads them from there rather than every
+// thread from global memory.
+struct TileInfo {
+    PassParams p;
+    int pair, tile, R0, C0;
+};
+
+// two buffers, the reduction scratch, two barriers, two tile descriptors
+constexpr int SMEM = 2 * BUF + NSUM * NT * 4 + 2 * 8 + 2 * (int)sizeof(TileInfo);
 
 using namespace ft_tma;
 
@@ -96,12 +107,20 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m)
                  : "memory");
 }
 
-// elected thread: copies of one tile of both frames into buffer `buf`
+// elected thread: copies of one tile of both frames into buffer `buf` (and, for a batch,
+// the tile's descriptor into `info`)
 template <bool GLOBAL_MAPS>
-__device__ __forceinline__ void issue_tile(const Loc &l, unsigned extra_tx, unsigned char *buf, uint64_t *bar)
+__device__ __forceinline__ void issue_tile(const Loc &l, unsigned extra_tx, unsigned char *buf, uint64_t *bar,
+                                           TileInfo *info)
 {
-    if (GLOBAL_MAPS)
+    if (GLOBAL_MAPS) {
         for (int k = 0; k < 4; ++k) tensormap_acquire(l.m + k);
+        info->p = *l.p;
+        info->pair = l.pair;
+        info->tile = l.tile;
+        info->R0 = l.R0;
+        info->C0 = l.C0;
+    }
     // generic-proxy reads of this buffer (previous tile) are ordered before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, TX + extra_tx);
@@ -234,14 +253,16 @@ __device__ __forceinline__ float2 unscale_block(float2 v)
 }
 
 template <bool EDGE>
-__device__ __forceinline__ void store_u16(unsigned char *img, int64_t pitch, int r1, int c, float t0, float t1,
-                                          int Hn, int Wn)
+__device__ __forceinline__ void store_u16(const PassParams &p, unsigned char *img, int64_t pitch, int r1, int c,
+                                          float t0, float t1, int Hn, int Wn)
 {
-    if (EDGE && r1 >= Hn) return;
+    if (EDGE && (r1 >= Hn || c >= Wn)) return;
+    const bool two = !EDGE || c + 1 < Wn;
     unsigned short *row = reinterpret_cast<unsigned short *>(img + (int64_t)r1 * pitch);
+    if (FT_CHECK && !in_extent(p, img, row + c, two ? 4 : 2, p.next_bytes)) return;
     const uint32_t lo = __float_as_uint(t0) & 0xffffu, hi = __float_as_uint(t1) << 16;
-    if (!EDGE || c + 1 < Wn) *reinterpret_cast<uint32_t *>(row + c) = lo | hi;
-    else if (c < Wn) row[c] = (unsigned short)lo;
+    if (two) *reinterpret_cast<uint32_t *>(row + c) = lo | hi;
+    else row[c] = (unsigned short)lo;
 }
 
 // One tile of 64 x 256 cubes.  A thread's packed pair of lanes normally holds the same
@@ -305,12 +326,12 @@ __device__ __forceinline__ void tile_body(const PassParams &p, const unsigned ch
                 const int r1 = (gr0 >> 1) + (r >> 1), r2 = r1 + DR / 2;
                 const int cl = gcl >> 1, cr = gcr >> 1;
                 const float2 v0 = unscale_block(add2(hb[0], b0)), v1 = unscale_block(add2(hb[1], b1));
-                store_u16<MASK>(ncur, p.next_pitch, r1, cl, v0.x, v1.x, Hn, Wn);
-                store_u16<MASK>(ncur, p.next_pitch, r2, cr, v0.y, v1.y, Hn, Wn);
+                store_u16<MASK>(p, ncur, p.next_pitch, r1, cl, v0.x, v1.x, Hn, Wn);
+                store_u16<MASK>(p, ncur, p.next_pitch, r2, cr, v0.y, v1.y, Hn, Wn);
                 if (wprev) {
                     const float2 u0 = unscale_block(add2(ha[0], a0)), u1 = unscale_block(add2(ha[1], a1));
-                    store_u16<MASK>(nprev, p.next_pitch, r1, cl, u0.x, u1.x, Hn, Wn);
-                    store_u16<MASK>(nprev, p.next_pitch, r2, cr, u0.y, u1.y, Hn, Wn);
+                    store_u16<MASK>(p, nprev, p.next_pitch, r1, cl, u0.x, u1.x, Hn, Wn);
+                    store_u16<MASK>(p, nprev, p.next_pitch, r2, cr, u0.y, u1.y, Hn, Wn);
                 }
             }
         }
@@ -325,6 +346,7 @@ ttc_pass_tma_kernel(const __grid_constant__ Items items, int *status, unsigned e
     unsigned char *bufs = smem;
     float *red = reinterpret_cast<float *>(smem + 2 * BUF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * BUF + NSUM * NT * 4);
+    TileInfo *info = reinterpret_cast<TileInfo *>(smem + 2 * BUF + NSUM * NT * 4 + 2 * 8);
     const int tid = threadIdx.x;
     const int total = items.total;
     // the copy engine writes 128-byte aligned boxes; refuse (and report) otherwise
@@ -342,7 +364,7 @@ ttc_pass_tma_kernel(const __grid_constant__ Items items, int *status, unsigned e
     if (tid == 0 && t0 < total) {
         Loc l;
         items.locate(t0, l);
-        issue_tile<GLOBAL_MAPS>(l, extra_tx, bufs, &bar[0]);
+        issue_tile<GLOBAL_MAPS>(l, extra_tx, bufs, &bar[0], &info[0]);
     }
 
     int k = 0;
@@ -353,7 +375,7 @@ ttc_pass_tma_kernel(const __grid_constant__ Items items, int *status, unsigned e
         if (tid == 0 && tn < total) {
             Loc ln;
             items.locate(tn, ln);
-            issue_tile<GLOBAL_MAPS>(ln, extra_tx, bufs + (b ^ 1) * BUF, &bar[b ^ 1]);
+            issue_tile<GLOBAL_MAPS>(ln, extra_tx, bufs + (b ^ 1) * BUF, &bar[b ^ 1], &info[b ^ 1]);
         }
         const bool ok = mbar_wait(&bar[b], (k >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -366,7 +388,15 @@ ttc_pass_tma_kernel(const __grid_constant__ Items items, int *status, unsigned e
             return;
         }
         Loc l;
-        items.locate(t, l);
+        if (GLOBAL_MAPS) {
+            l.p = &info[b].p;
+            l.pair = info[b].pair;
+            l.tile = info[b].tile;
+            l.R0 = info[b].R0;
+            l.C0 = info[b].C0;
+        } else {
+            items.locate(t, l);
+        }
         const PassParams &p = *l.p;
         float2 acc2[NSUM];
 #pragma unroll

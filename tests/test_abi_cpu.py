@@ -205,3 +205,21 @@ def test_fastconv_separable_validation(L):
     assert L.fastconv_separable(f, dims, 2, facs, kd, ctypes.c_void_p(48), None, None) == 1  # no scratch
     assert L.fastconv_separable(f, dims, 2, facs, kd, ctypes.c_void_p(48), ctypes.c_void_p(48), None) == 1
     assert L.fastconv_separable(f, dims, 9, facs, kd, ctypes.c_void_p(48), ctypes.c_void_p(64), None) == 2
+
+
+def test_checked_build_flag_plumbing(monkeypatch):
+    """FASTTTC_CHECK selects the checked build's define, and the record flag it reports has the
+    same value in the header and the binding."""
+    import re
+    from paper_1612_08825_gb300 import build as b
+    monkeypatch.delenv("FASTTTC_CHECK", raising=False)
+    assert b.extra_flags() == []
+    monkeypatch.setenv("FASTTTC_CHECK", "1")
+    assert b.extra_flags() == ["-DFT_CHECK=1"]
+    monkeypatch.setenv("FASTTTC_CHECK", "0")
+    assert b.extra_flags() == []
+    hdr = open(os.path.join(ROOT, "include", "fastttc.h")).read()
+    m = re.search(r"#define FT_FLAG_BOUNDS (\d+)", hdr)
+    assert m and int(m.group(1)) == ft.FLAG_BOUNDS
+    flags = [int(v) for v in re.findall(r"#define FT_FLAG_\w+ (\d+)", hdr)]
+    assert len(set(flags)) == len(flags) and all(f & (f - 1) == 0 for f in flags)   # distinct bits
