@@ -266,6 +266,9 @@ size_t ttc_ctx_workspace_bytes(const ttc_ctx *ctx);
  *   out : device, `levels` results, out[l] for level l.
  * Per-cube products are formed in FP32 and summed pairwise in FP32 within each
  * tile; tiles are merged in FP64 in a fixed order (results are deterministic).
+ * uint8 frames of 2..5 levels with 16-byte aligned frames and pitch take the
+ * all-levels kernel (one launch for every level, then the merge/solve); other
+ * requests take one pass per level.
  * Errors: FT_ERR_INVALID_ARG, FT_ERR_SHAPE (a level smaller than 2 x 2, pitch),
  * FT_ERR_UNSUPPORTED (levels > FT_MAX_LEVELS), FT_ERR_WORKSPACE (request larger
  * than the context), FT_ERR_CUDA.
@@ -330,6 +333,10 @@ ft_status ttc_gradient_batch(const void *images, int n, int64_t image_stride_byt
  * The same for the T-1 consecutive pairs (t, t+1) of a video of T frames stored
  * frame_stride_bytes apart: out[(t * levels) + l] for pair t, level l (device,
  * (T-1) * levels results).  Sec. V-B: the estimate is produced at every frame.
+ * A video whose pairs give more than 64 level-0 tiles of 64 x 256 cubes per CTA of
+ * the grid (two per SM) takes one pass per level, each frame's pyramid built once;
+ * shorter ones take the all-levels kernel under the conditions of ttc_solve (results
+ * of the two agree within rounding; the choice depends only on the request).
  */
 ft_status ttc_solve_sequence(ttc_ctx *ctx, const void *frames, int64_t frame_stride_bytes, int T,
                              int dtype, int H, int W, int64_t pitch_bytes, int levels, int mode,
@@ -390,12 +397,16 @@ ft_status ttc_reduce_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, void *
  * many cameras at once).  ttc_batch_prepare takes the pairs (host array of
  * descriptors; the frames are device memory owned by the caller and must stay valid
  * and unchanged in address until the last ttc_batch_run that uses them), checks them,
- * lays out the context workspace, and uploads a work list of (pair, level, tile)
- * items and per-(pair, level) descriptors on `stream`.  ttc_batch_run then performs,
- * for every pair and level, the same computation as ttc_solve (same results up to
- * rounding; identical for a pair alone or in any batch with the same tile plan) with
- * two kernel launches per level over the work list plus one merge/solve launch; it
- * only launches kernels, so a caller may capture it in a CUDA graph and replay it.
+ * lays out the context workspace, and uploads a work list and per-pair descriptors on
+ * `stream`.  ttc_batch_run then performs, for every pair and level, the same
+ * computation as ttc_solve (same results up to rounding; identical for a pair alone
+ * or in any batch with the same tile plan).  uint8 pairs of 2..5 levels whose frames
+ * and pitch are 16-byte aligned take one launch of the all-levels kernel (every level
+ * of every such pair, work list of strips of level-0 tiles; the tile plan does not
+ * apply to them, and their results equal those of ttc_solve bitwise); other pairs
+ * take two launches per level; one merge/solve launch follows.  It only launches
+ * kernels (after zeroing the context's status word), so a caller may capture it in a
+ * CUDA graph and replay it.
  * out: device, npairs * levels results, out[p * levels + l].
  * ttc_batch_autotune times, on the prepared batch, 64-row and 16-row tiles for every
  * level, keeps the faster per level for later prepares on this context, prepares
@@ -412,11 +423,13 @@ typedef struct {
     int64_t pitch_bytes;
     /* Per-frame pyramids owned by the caller (both nullable; see ttc_pyramid_layout).
      * prev_pyramid: levels 1 .. levels-1 of `prev`, as an earlier ttc_batch_run wrote
-     * them into a cur_pyramid of the same H, W, dtype and levels; read only.
+     * them into a cur_pyramid of the same H, W, dtype and levels; read only (pairs of
+     * the all-levels kernel form every level from the frames and do not read it).
      * cur_pyramid: receives levels 1 .. levels-1 of `cur`.  A null pointer puts that
-     * frame's pyramid in the context workspace instead.  The two must differ, and no
-     * block may be one pair's cur_pyramid and another pair's prev_pyramid in the same
-     * batch (the results of such a batch are unspecified).  16-byte aligned. */
+     * frame's pyramid in the context workspace instead (or nowhere, for pairs of the
+     * all-levels kernel).  The two must differ, and no block may be one pair's
+     * cur_pyramid and another pair's prev_pyramid in the same batch (the results of
+     * such a batch are unspecified).  16-byte aligned. */
     const void *prev_pyramid;
     void *cur_pyramid;
 } ttc_pair_desc;

@@ -73,7 +73,7 @@ def build_checked_ttc(verbose: bool = False) -> str:
     """The TTC part of the library (ttc.cu, api.cu) built with FT_CHECK, in-tree as
     _lib/libfastttc_ttc_checked.so: for tests of the checked build."""
     out = os.path.join(OUT_DIR, "libfastttc_ttc_checked.so")
-    srcs = [os.path.join(CSRC, "ttc.cu"), os.path.join(CSRC, "api.cu")]
+    srcs = [os.path.join(CSRC, "ttc.cu"), os.path.join(CSRC, "ttc_fused.cu"), os.path.join(CSRC, "api.cu")]
     if os.path.exists(out) and all(os.path.getmtime(f) <= os.path.getmtime(out) for f in _deps()):
         return out
     _compile_and_link(srcs, ["-DFT_CHECK=1"], out, verbose)

@@ -13,11 +13,13 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "ttc_pass.cuh"
 #include "ttc_merge.cuh"
 #include "ttc_tma.cuh"
+#include "ttc_fused.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -286,6 +288,50 @@ void geometry(int H, int W, int levels, int dtype, int npairs, int nframes, Geom
     g.image_bytes = io;
 }
 
+// Geometry of the all-levels kernel: every level's partials on the level-0 tile grid
+// (64 x 256 cubes), no level images.
+void geometry_fused(int H, int W, int levels, int npairs, Geometry &g)
+{
+    g.levels = levels;
+    g.npairs = npairs;
+    g.nframes = 0;
+    const int tx = (int)ft::ceil_div(W - 1, TC), ty = (int)ft::ceil_div(H - 1, TR);
+    for (int l = 0; l < levels; ++l) {
+        g.H[l] = H >> l;
+        g.W[l] = W >> l;
+        g.tiles_x[l] = tx;
+        g.tiles_y[l] = ty;
+        g.ntiles[l] = tx * ty;
+        g.tr[l] = TR;
+        g.poff[l] = (int64_t)l * npairs * tx * ty * NSUM;
+        g.shift[l] = l <= 3 ? 16 : 0;     // levels 0..3: pixels scaled by 256 in the kernel's arithmetic
+        g.esize[l] = l == 0 ? 1 : 2;
+        g.pitch[l] = g.fstride[l] = g.ioff[l] = 0;
+    }
+    g.partial_floats = (int64_t)levels * npairs * tx * ty * NSUM;
+    g.image_bytes = 0;
+}
+
+// the all-levels kernel takes uint8 pairs of 2..5 levels whose frames the copy engine
+// can address (16-byte aligned frames, pitch and pair stride)
+bool fused_eligible(int dtype, int levels, const void *prev, const void *cur, int64_t pitch, int64_t pair_stride,
+                    int npairs)
+{
+    if (dtype != FT_U8 || levels < 2 || levels > ttc_fused::MAXLEV) return false;
+    if ((reinterpret_cast<uintptr_t>(prev) & 15) || (reinterpret_cast<uintptr_t>(cur) & 15) || (pitch & 15))
+        return false;
+    if (npairs > 1 && (pair_stride <= 0 || (pair_stride & 15))) return false;
+    return ft::tensor_map_encoder() != nullptr;
+}
+
+// cube centre offsets of level l: x = j + 1/2 - cx_l with cx_l = (W - 2^l) / 2^(l+1),
+// the level-0 image centre (W-1)/2 in level-l pixel indices
+float centre_off(int n, int l)
+{
+    const double pl = (double)(1 << l);
+    return (float)(0.5 - ((double)n - pl) / (2.0 * pl));
+}
+
 }  // namespace
 
 struct ttc_ctx {
@@ -306,8 +352,10 @@ struct ttc_ctx {
     SolveDesc *d_sdesc;               // [max_pairs * max_levels]
     CUtensorMap *d_maps;              // [max_pairs][4]: level-0 maps of pairs the TMA kernel takes
     int2 *d_items;                    // [items_cap]: (pair, tile) of the TMA kernel's level-0 items
+    ttc_fused::Geom *d_geoms;         // [max_pairs]: pairs of the all-levels kernel
+    int4 *d_units;                    // [items_cap]: its units (pair, strip, first tile row, tiles)
     size_t items_cap;
-    size_t off_maps, off_items;       // byte offsets of those arrays in the staging buffers
+    size_t off_maps, off_items, off_geoms, off_units;   // byte offsets of those arrays in the staging buffers
     unsigned char *h_stage;           // pinned staging buffer of the arrays
     size_t stage_bytes;
     cudaEvent_t stage_ev;             // the last upload from h_stage
@@ -317,6 +365,7 @@ struct ttc_ctx {
         int rpw[FT_MAX_LEVELS], in_es[FT_MAX_LEVELS], out_es[FT_MAX_LEVELS];
         int n_int[FT_MAX_LEVELS], n_edge[FT_MAX_LEVELS];
         int n_tma;                    // level-0 items of the TMA kernel (uint8 pairs it can read)
+        int n_units;                  // units of the all-levels kernel
         bool ready;
     } b;
     int plan_rpw[FT_MAX_LEVELS];      // tile rows per warp per level for batches (0: automatic)
@@ -350,7 +399,9 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     Geometry g, g16;
     geometry(max_H, max_W, lv, FT_F32, max_pairs, 2 * max_pairs, g, TR);
     geometry(max_H, max_W, lv, FT_F32, max_pairs, 2 * max_pairs, g16, ttc_pass::TR_SMALL);
-    const int64_t pf = std::max(g.partial_floats, g16.partial_floats);
+    Geometry gf;
+    geometry_fused(max_H, max_W, std::min(lv, ttc_fused::MAXLEV), max_pairs, gf);
+    const int64_t pf = std::max(std::max(g.partial_floats, g16.partial_floats), gf.partial_floats);
     const int64_t ib = std::max(g.image_bytes, g16.image_bytes);
     float *part = nullptr;
     unsigned char *img = nullptr;
@@ -390,7 +441,9 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->items_cap = tiles0 * (size_t)max_pairs;
     c->off_maps = (b_desc + b_pre + b_sd + 127) / 128 * 128;
     c->off_items = c->off_maps + (size_t)max_pairs * 4 * sizeof(CUtensorMap);
-    c->stage_bytes = c->off_items + c->items_cap * sizeof(int2);
+    c->off_geoms = (c->off_items + c->items_cap * sizeof(int2) + 127) / 128 * 128;
+    c->off_units = (c->off_geoms + (size_t)max_pairs * sizeof(ttc_fused::Geom) + 127) / 128 * 128;
+    c->stage_bytes = c->off_units + c->items_cap * sizeof(int4);
     unsigned char *dbuf = nullptr;
     e = cudaMalloc(&dbuf, c->stage_bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(&c->h_stage, c->stage_bytes, cudaHostAllocDefault);
@@ -422,6 +475,8 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->d_sdesc = reinterpret_cast<SolveDesc *>(dbuf + b_desc + b_pre);
     c->d_maps = reinterpret_cast<CUtensorMap *>(dbuf + c->off_maps);
     c->d_items = reinterpret_cast<int2 *>(dbuf + c->off_items);
+    c->d_geoms = reinterpret_cast<ttc_fused::Geom *>(dbuf + c->off_geoms);
+    c->d_units = reinterpret_cast<int4 *>(dbuf + c->off_units);
     c->bytes += c->stage_bytes;
     *ctx = c;
     if (!c->ring_ready) {
@@ -552,6 +607,99 @@ cudaError_t launch_pass(const ttc_pass::PassParams &p, int out_esize, int npairs
     return ttc_pass::launch<Tin, float>(p, npairs, s, count);
 }
 
+// Long videos (consecutive pairs sharing frames) keep the per-level passes: there each
+// frame's pyramid is built once and the level-0 pass runs alone, which measured faster
+// than the all-levels kernel once a video gives every CTA of the grid more than 64
+// level-0 tiles (1080p, 299 pairs: 1.10 against 1.16 ms per step).  Decided on the pair
+// count of the whole sequence, so that the chunks of a host sequence take the same path.
+int sm_count();
+bool per_level_video(int independent, int seq_pairs, int H, int W)
+{
+    if (independent) return false;
+    const int64_t tiles = (int64_t)seq_pairs * ft::ceil_div(W - 1, TC) * ft::ceil_div(H - 1, TR);
+    return tiles > 64 * 2 * (int64_t)sm_count();
+}
+
+// SM count of the current device (grid sizes of the persistent kernels)
+int sm_count()
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(nsm, 1);
+}
+
+// Tiles per unit of the all-levels kernel: whole strips when there are at least four
+// units per CTA of the grid, else shorter runs (each below the top of its strip starts
+// with a prologue).
+int fused_segment(int64_t strips, int tiles_y)
+{
+    const int64_t per = strips * tiles_y / (4 * 2 * (int64_t)sm_count());
+    return (int)std::min<int64_t>(tiles_y, std::max<int64_t>(1, per));
+}
+
+void fused_geom(ttc_fused::Geom &fg, const Geometry &g, int H, int W, int levels, float *partials)
+{
+    fg = ttc_fused::Geom{};
+    fg.H = H;
+    fg.W = W;
+    fg.tiles_x = g.tiles_x[0];
+    fg.tiles_y = g.tiles_y[0];
+    fg.ntiles = g.ntiles[0];
+    fg.nlev = levels;
+    for (int l = 0; l < levels; ++l) {
+        fg.xoff[l] = centre_off(W, l);
+        fg.yoff[l] = centre_off(H, l);
+        fg.part[l] = partials + g.poff[l];
+    }
+}
+
+// All levels of npairs uint8 pairs by the all-levels kernel (pair p is (prev + p *
+// pair_stride, cur + p * pair_stride)).  False when the frames' tensor maps cannot be
+// made (the caller then takes the per-level passes); *st is the call's status otherwise.
+bool launch_fused(ttc_ctx *ctx, const void *prev, const void *cur, int64_t pair_stride, int npairs, int H, int W,
+                  int64_t pitch, int levels, cudaStream_t s, ft_status *st)
+{
+    Geometry g;
+    geometry_fused(H, W, levels, npairs, g);
+    *st = FT_OK;
+    const int64_t ps = npairs == 1 ? (pitch * H + 15) / 16 * 16 : pair_stride;
+    ttc_fused::VideoUnits u{};
+    if (!u8_frame_map(&u.m[0], prev, W, H, npairs, pitch, ps, ttc_tma::BW) ||
+        !u8_frame_map(&u.m[1], cur, W, H, npairs, pitch, ps, ttc_tma::BW) ||
+        !u8_frame_map(&u.m[2], prev, W, H, npairs, pitch, ps, ttc_tma::XW) ||
+        !u8_frame_map(&u.m[3], cur, W, H, npairs, pitch, ps, ttc_tma::XW))
+        return false;
+    if (g.partial_floats > ctx->partial_cap) {
+        *st = FT_ERR_WORKSPACE;
+        return true;
+    }
+    fused_geom(u.g, g, H, W, levels, ctx->partials);
+    u.npairs = npairs;
+    u.seg = fused_segment((int64_t)npairs * u.g.tiles_x, u.g.tiles_y);
+    u.nseg = (int)ft::ceil_div(u.g.tiles_y, u.seg);
+    const int64_t total = (int64_t)npairs * u.g.tiles_x * u.nseg;
+    if (total > 0x7fffffffLL) {
+        *st = FT_ERR_UNSUPPORTED;
+        return true;
+    }
+    u.total = (int)total;
+    // the status word and the unit ticket start at zero
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess && ctx->ev0_start) e = cudaEventRecord(ctx->ev0_start, s);
+    if (e == cudaSuccess) e = ttc_fused::launch_video(u, ctx->status, ctx->status + 1, s);
+    if (e == cudaSuccess && ctx->ev0_end) e = cudaEventRecord(ctx->ev0_end, s);
+    if (e != cudaSuccess) {
+        ft::set_cuda_error(e);
+        *st = FT_ERR_CUDA;
+        return true;
+    }
+    ctx->g = g;
+    ctx->ready = true;
+    ctx->launches = 1;
+    return true;
+}
+
 // all levels of npairs pairs: pair p is (prev + p * pair_stride, cur + p * pair_stride);
 // independent = 0 for the consecutive pairs of a video (frame t+1 shared)
 // the levels kernel takes levels 1 .. L-1 in one launch when their images have one pixel
@@ -569,6 +717,10 @@ ft_status launch_partials(ttc_ctx *ctx, const void *prev, const void *cur, int64
     if ((st = check_levels(H, W, levels)) != FT_OK) return st;
     if (npairs > ctx->max_pairs || levels > ctx->max_levels || H > ctx->max_H || W > ctx->max_W)
         return FT_ERR_WORKSPACE;
+    if (fused_eligible(dtype, levels, prev, cur, pitch, pair_stride, npairs) &&
+        !per_level_video(independent, plan_pairs ? plan_pairs : npairs, H, W)) {
+        if (launch_fused(ctx, prev, cur, pair_stride, npairs, H, W, pitch, levels, s, &st)) return st;
+    }
     Geometry g;
     geometry(H, W, levels, dtype, npairs, independent ? 2 * npairs : npairs + 1, g, 0, plan_pairs);
     if (g.partial_floats > ctx->partial_cap || g.image_bytes > ctx->image_cap) return FT_ERR_WORKSPACE;
@@ -784,6 +936,17 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
     int64_t poff = 0, ioff = 0;
     int in_es[FT_MAX_LEVELS], out_es[FT_MAX_LEVELS];
     int64_t n_int[FT_MAX_LEVELS] = {0}, n_edge[FT_MAX_LEVELS] = {0};
+    // uint8 pairs of 2..5 levels whose frames the copy engine can address take the
+    // all-levels kernel (any tile plan: its tiles are fixed); a caller's first-frame
+    // pyramid is not read (the kernel forms every level from level 0, giving the same
+    // block sums), the second frame's pyramid is written when a block is given
+    ttc_fused::Geom *hgeoms = reinterpret_cast<ttc_fused::Geom *>(ctx->h_stage + ctx->off_geoms);
+    int4 *hunits = reinterpret_cast<int4 *>(ctx->h_stage + ctx->off_units);
+    const bool fused_dt = dtype == FT_U8 && levels >= 2 && levels <= ttc_fused::MAXLEV &&
+                          ft::tensor_map_encoder() != nullptr;
+    int n_fused = 0;
+    int64_t fused_tiles = 0;
+    std::vector<int> fused_pairs;
     // per pair: level images and partials, level by level.  A frame's level images
     // live in the caller's pyramid block when the descriptor gives one, else in the
     // context workspace (images + ioff).
@@ -793,6 +956,7 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
         int64_t prev_off[FT_MAX_LEVELS], cur_off[FT_MAX_LEVELS];   // workspace offsets, -1: caller block
         int64_t pyr_off[FT_MAX_LEVELS];                             // offsets in a pyramid block
         int64_t po = 0;
+        const int64_t ioff_pair = ioff;
         for (int l = 1; l < levels; ++l) {
             batch_level_image(d.H, d.W, l, dtype, &img_pitch[l], &img_fs[l]);
             pyr_off[l] = po;
@@ -809,8 +973,52 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
             return cur_off[l] >= 0 ? ctx->images + cur_off[l]
                                    : static_cast<unsigned char *>(d.cur_pyramid) + pyr_off[l];
         };
-        bool tma = tma_level0 && (reinterpret_cast<uintptr_t>(d.prev) & 15) == 0 &&
-                   (reinterpret_cast<uintptr_t>(d.cur) & 15) == 0 && (d.pitch_bytes & 15) == 0;
+        const bool aligned16 = (reinterpret_cast<uintptr_t>(d.prev) & 15) == 0 &&
+                               (reinterpret_cast<uintptr_t>(d.cur) & 15) == 0 && (d.pitch_bytes & 15) == 0;
+        if (fused_dt && aligned16) {
+            const int64_t ps = (d.pitch_bytes * d.H + 15) / 16 * 16;
+            bool ok = u8_frame_map(&hmaps[4 * p + 0], d.prev, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::BW) &&
+                      u8_frame_map(&hmaps[4 * p + 1], d.cur, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::BW) &&
+                      u8_frame_map(&hmaps[4 * p + 2], d.prev, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::XW) &&
+                      u8_frame_map(&hmaps[4 * p + 3], d.cur, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::XW);
+            if (ok) {
+                Geometry gf;
+                geometry_fused(d.H, d.W, levels, 1, gf);
+                fused_geom(hgeoms[p], gf, d.H, d.W, levels, ctx->partials + poff);
+                if (d.cur_pyramid) {
+                    hgeoms[p].pyr = static_cast<unsigned char *>(d.cur_pyramid);
+                    for (int l = 1; l < levels; ++l) {
+                        hgeoms[p].pyr_off[l] = pyr_off[l];
+                        hgeoms[p].pyr_pitch[l] = img_pitch[l];
+                    }
+                }
+                // the per-level kernels skip this pair: empty item ranges, unused descriptors
+                for (int l = 0; l < levels; ++l) {
+                    hd[(size_t)l * ctx->max_pairs + p] = ttc_pass::PassParams{};
+                    int *pi = hpre + ((size_t)l * 2 + 0) * (ctx->max_pairs + 1);
+                    int *pe = hpre + ((size_t)l * 2 + 1) * (ctx->max_pairs + 1);
+                    pi[p] = pi[p + 1] = (int)n_int[l];
+                    pe[p] = pe[p + 1] = (int)n_edge[l];
+                    SolveDesc sd;
+                    sd.poff = poff + gf.poff[l];
+                    sd.ncubes = (int64_t)(gf.H[l] - 1) * (gf.W[l] - 1);
+                    sd.ntiles = gf.ntiles[l];
+                    sd.level = l;
+                    sd.shift = gf.shift[l];
+                    hsd[(size_t)p * levels + l] = sd;
+                    in_es[l] = l == 0 ? es0 : 2;
+                    out_es[l] = l + 1 <= 4 ? 2 : 4;
+                }
+                poff += gf.partial_floats;
+                // this pair's level images were counted in the workspace: give them back
+                ioff = ioff_pair;
+                fused_pairs.push_back(p);
+                fused_tiles += gf.ntiles[0];
+                ++n_fused;
+                continue;
+            }
+        }
+        bool tma = tma_level0 && aligned16;
         if (tma) {
             const int64_t ps = (d.pitch_bytes * d.H + 15) / 16 * 16;
             tma = u8_frame_map(&hmaps[4 * p + 0], d.prev, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::BW) &&
@@ -888,16 +1096,39 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
         }
     }
     if (poff > ctx->partial_cap || ioff > ctx->image_cap) return FT_ERR_WORKSPACE;
+    // units of the all-levels kernel: strips cut into runs of `seg` tiles, longest first
+    // (the kernel hands them out in order, so the long ones start early)
+    int64_t n_units = 0;
+    if (n_fused > 0) {
+        int max_ty = 1;
+        for (int p : fused_pairs) max_ty = std::max(max_ty, hgeoms[p].tiles_y);
+        const int seg = (int)std::min<int64_t>(max_ty, std::max<int64_t>(1, fused_tiles / (8 * (int64_t)sm_count())));
+        for (int p : fused_pairs) {
+            const ttc_fused::Geom &fg = hgeoms[p];
+            for (int tx = 0; tx < fg.tiles_x; ++tx)
+                for (int j0 = 0; j0 < fg.tiles_y; j0 += seg) {
+                    if (n_units >= (int64_t)ctx->items_cap) return FT_ERR_WORKSPACE;
+                    hunits[n_units++] = make_int4(p, tx, j0, std::min(seg, fg.tiles_y - j0));
+                }
+        }
+        std::stable_sort(hunits, hunits + n_units, [](const int4 &a, const int4 &b) { return a.w > b.w; });
+    }
     for (int l = 0; l < levels; ++l)
         if (n_int[l] > 0x7fffffffLL || n_edge[l] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
     if (n_tma > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
     unsigned char *dstage = reinterpret_cast<unsigned char *>(ctx->d_descs);
     cudaError_t e = cudaMemcpyAsync(dstage, ctx->h_stage, ctx->off_maps, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n_tma > 0)
+    if (e == cudaSuccess && (n_tma > 0 || n_units > 0))
         e = cudaMemcpyAsync(dstage + ctx->off_maps, ctx->h_stage + ctx->off_maps,
                             (size_t)npairs * 4 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n_tma > 0)
         e = cudaMemcpyAsync(dstage + ctx->off_items, ctx->h_stage + ctx->off_items, (size_t)n_tma * sizeof(int2),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_units > 0)
+        e = cudaMemcpyAsync(dstage + ctx->off_geoms, ctx->h_stage + ctx->off_geoms,
+                            (size_t)npairs * sizeof(ttc_fused::Geom), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_units > 0)
+        e = cudaMemcpyAsync(dstage + ctx->off_units, ctx->h_stage + ctx->off_units, (size_t)n_units * sizeof(int4),
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev, s);
     if (e != cudaSuccess) {
@@ -911,6 +1142,7 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
     ctx->b.levels = levels;
     ctx->b.dtype = dtype;
     ctx->b.n_tma = (int)n_tma;
+    ctx->b.n_units = (int)n_units;
     for (int l = 0; l < levels; ++l) {
         ctx->b.rpw[l] = rpw[l];
         ctx->b.in_es[l] = in_es[l];
@@ -945,7 +1177,13 @@ ft_status batch_run_impl(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStre
     if (!ctx->b.ready) return FT_ERR_INVALID_ARG;
     const auto &b = ctx->b;
     int count = 0;
-    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(int), s);
+    // the status word and the all-levels kernel's unit ticket start at zero
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess && b.n_units > 0) {
+        const ttc_fused::BatchUnits u{ctx->d_geoms, ctx->d_maps, ctx->d_units, b.n_units};
+        e = ttc_fused::launch_batch(u, ctx->status, ctx->status + 1, s);
+        ++count;
+    }
     for (int l = 0; l < b.levels && e == cudaSuccess; ++l) {
         if (l == 0 && b.n_tma > 0) {
             ttc_tma::BatchItems it{ctx->d_descs, ctx->d_maps, ctx->d_items, b.n_tma};
@@ -1151,10 +1389,12 @@ extern "C" ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dt
     ft_status st = check_frames(dtype, H, W, pitch_bytes);
     if (st != FT_OK) return st;
     if ((st = check_levels(H, W, levels)) != FT_OK) return st;
-    Geometry g;
+    Geometry g, gf;
     geometry(H, W, levels, dtype, 1, 2, g);
-    // layout: 256 bytes for the status word, the partials, the level images
-    const int64_t pbytes = 256 + (g.partial_floats * (int64_t)sizeof(float) + 255) / 256 * 256;
+    geometry_fused(H, W, std::min(levels, ttc_fused::MAXLEV), 1, gf);
+    const int64_t pfl = std::max(g.partial_floats, gf.partial_floats);
+    // layout: 256 bytes for the status word and unit ticket, the partials, the level images
+    const int64_t pbytes = 256 + (pfl * (int64_t)sizeof(float) + 255) / 256 * 256;
     if (pbytes + g.image_bytes > (int64_t)FT_NOALLOC_SCRATCH_BYTES) return FT_ERR_WORKSPACE;
     unsigned char *base = nullptr;
     if ((st = noalloc_scratch(&base)) != FT_OK) return st;
@@ -1167,7 +1407,7 @@ extern "C" ft_status ttc_solve_noalloc(const void *prev, const void *cur, int dt
     c.status = reinterpret_cast<int *>(base);
     c.partials = reinterpret_cast<float *>(base + 256);
     c.images = base + pbytes;
-    c.partial_cap = g.partial_floats;
+    c.partial_cap = pfl;
     c.image_cap = g.image_bytes;
     c.bytes = FT_NOALLOC_SCRATCH_BYTES;
     c.ready = false;

@@ -258,24 +258,23 @@ def test_full_size_1080p_five_levels():
 
 
 def test_full_size_video_large_tile_paths():
-    """35 consecutive 1080p pairs: level 0 by the copy-engine pass, levels 1-4 by the
-    load-based pass (64-row tiles at level 1, 16-row tiles below); sampled pairs against
-    the oracle, and the single-pair entry point (16-row tiles at levels >= 1) within
-    tolerance of the video."""
+    """35 consecutive 1080p pairs: all five levels in one launch of the all-levels kernel
+    (strips cut into units of three tiles, so units below the top of a strip run the
+    prologue), then the merge/solve; sampled pairs against the oracle, and the
+    single-pair entry point (one-tile units) bitwise equal to the video."""
     sc = scenes.tilted_plane_scene(H=1080, W=1920, seed=2031)
     fr = scenes.render_sequence(sc, 36, device=DEV)
     ctx = ft.TtcContext(1080, 1920, 5, 35)
     got = ft.results_to_numpy(ctx.solve_sequence(fr, levels=5, mode=1)).reshape(35, 5)
-    # level 0 by the copy-engine pass; levels 1-4 one launch per tile set; the merge/solve
-    assert 3 <= ctx.last_launch_count <= 9
+    # the all-levels kernel and the merge/solve
+    assert ctx.last_launch_count == 2
     host = fr.cpu().numpy()
     for t in (0, 17, 34):
         ref = oracle.ttc_pair(host[t], host[t + 1], levels=5, mode=1)
         for l in range(5):
             check_record(got[t, l], ref[l], 1, l)
         one = ft.results_to_numpy(ctx.solve(fr[t], fr[t + 1], levels=5, mode=1))
-        for l in range(5):
-            check_record(one[l], ref[l], 1, l)
+        assert one.tobytes() == got[t].tobytes()
     ctx.close()
 
 
