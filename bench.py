@@ -21,8 +21,9 @@ Also reported in the same JSON line:
                  the HBM or FP32 FMA roof, L2 flushed between runs; separable Gaussians
                  through one 1-D pass per axis against the direct path
   gradient       gradient magnitude and direction of 1080p uint8 images, GB/s
-  batch_uneven   512 independent pairs of uneven sizes in one batch (work-list
-                 launches, CUDA graph) against the per-frame path
+  batch_uneven   512 independent pairs of uneven sizes in one batch (the all-levels
+                 kernel and the merge/solve, replayed from a CUDA graph) against the
+                 per-frame path, with every pair's error against the FP64 oracle
   serve          64 camera streams replayed at 30 fps through the serving loop and
                  through the per-frame path (p50/p99 latency), then saturated
   accuracy       TTC/FOE mean squared error against ground truth per level and per
@@ -447,6 +448,7 @@ def batch_bench(dev, args):
         buf[:, :, :w] = fr
         pairs.append((buf[0, :, :w], buf[1, :, :w]))
     px = sum(h * w for h, w, _, _ in specs)
+    cubes = sum(((h >> l) - 1) * ((w >> l) - 1) for h, w, _, _ in specs for l in range(LEVELS))
     ctx = ft.TtcContext(1080, 1920, LEVELS, n, device=dev)
     ctx.batch_prepare(pairs, levels=LEVELS)
     out = ctx.new_results(n * LEVELS)
@@ -459,6 +461,7 @@ def batch_bench(dev, args):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         ctx.batch_run(mode=ft.MODE_FOE, out=out)
+    launches = ctx.last_launch_count
     for _ in range(3):
         g.replay()
     torch.cuda.synchronize(dev)
@@ -495,6 +498,9 @@ def batch_bench(dev, args):
     return {"workload": f"{n} independent uint8 pairs, W 160-1920, H 120-1080, {LEVELS} levels, FOE, "
                         "rows pitched to 64 bytes",
             "megapixels_per_frame_set": px / 1e6, "rows_per_tile_per_level": rows,
+            "launches_per_batch": launches, "cubes_per_batch": cubes,
+            "cubes_per_s": cubes / t_graph,
+            "fp32_issue_frac": cubes * OPS_PER_CUBE0 / t_graph / alu_roof(dev),
             "graph_pairs_per_s": n / t_graph, "graph_ms_per_batch": t_graph * 1e3,
             "per_frame_path_pairs_per_s": n / t_single, "per_frame_path_ms": t_single * 1e3,
             "speedup_vs_per_frame_path": t_single / t_graph,
@@ -649,6 +655,13 @@ OPS_PER_CUBE0 = 23.5
 # of the same kernel on an 80-frame video (287.9 MB for 79 pairs: 3.64 MB per pair,
 # scaled by pairs)
 L0_TRAFFIC_PER_PAIR = 3.64e6
+
+
+def alu_roof(dev):
+    """FP32 issue roof in lane-ops/s: SMs x 128 FP32 lanes x the maximum SM clock."""
+    import torch
+    _, sm_max, _ = _peaks()
+    return torch.cuda.get_device_properties(dev).multi_processor_count * 128 * sm_max * 1e6
 
 
 def conv_hbm_summary(rows, hbm_peak):
