@@ -388,46 +388,28 @@ conv_direct_kernel(const ConvParams p, int64_t total)
 // once per warp up front (16-byte loads; all loads in flight together); the KC - 1
 // columns to the left come from lane l - 1 by shuffle (lane 0 loads them).  The KR
 // previous rows of each of the KL input planes stay in registers.
+// Grid: x = groups of 8 warps within a plane (a warp per strip x row block, row blocks
+// fastest), y and z = the output plane (z counts 65535 planes), so that a warp finds its
+// work with one 32-bit division and its input planes without any (lead_plane).
 template <int KL, int KR, int KC, int RB>
 __global__ void __launch_bounds__(kThreads)
-conv_rows_kernel(const ConvParams p, int64_t nstrips, int64_t nrb, int64_t total_warps)
+conv_rows_kernel(const ConvParams p, int nrb, int warps_per_plane, int64_t planes)
 {
     constexpr int NROW = RB + KR - 1;            // input rows per warp
     constexpr int WN = KC + 3;                   // window: KC - 1 halo + 4 own columns
     const int lane = threadIdx.x & 31;
-    const int64_t wg = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    if (wg >= total_warps) return;               // warp-uniform
-    const int64_t plane = wg / (nstrips * nrb);
-    const int64_t rem = wg - plane * nstrips * nrb;
-    const int64_t strip = rem / nrb;
-    const int64_t m0 = (rem - strip * nrb) * RB;
-    const int64_t ox0 = strip * 128;
+    const int wi = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int64_t plane = (int64_t)blockIdx.z * 65535 + blockIdx.y;
+    if (wi >= warps_per_plane || plane >= planes) return;      // warp-uniform
+    const int strip = wi / nrb;
+    const int64_t m0 = (int64_t)(wi - strip * nrb) * RB;
+    const int64_t ox0 = (int64_t)strip * 128;
     const int64_t c0 = ox0 + 4 * lane;
 
     // input plane of each leading kernel index (-1: outside the input)
     int64_t q[KL];
-    {
-        int64_t pm[FT_MAX_NDIM];
-        int64_t r = plane;
-        for (int d = p.nlead - 1; d >= 0; --d) {
-            pm[d] = r % p.out_lead[d];
-            r /= p.out_lead[d];
-        }
 #pragma unroll
-        for (int R = 0; R < KL; ++R) {
-            int64_t qq = 0, rr = R, stride = 1;
-            bool inside = true;
-            for (int d = p.nlead - 1; d >= 0; --d) {
-                const int64_t rd = rr % p.k_lead[d];
-                rr /= p.k_lead[d];
-                const int64_t qd = pm[d] - rd;
-                if (qd < 0 || qd >= p.in_lead[d]) inside = false;
-                qq += qd * stride;
-                stride *= p.in_lead[d];
-            }
-            q[R] = inside ? qq : -1;
-        }
-    }
+    for (int R = 0; R < KL; ++R) q[R] = lead_plane(p, plane, R);
     float kr[KL][KR][KC];
 #pragma unroll
     for (int R = 0; R < KL; ++R)
@@ -509,13 +491,16 @@ conv_rows_kernel(const ConvParams p, int64_t nstrips, int64_t nrb, int64_t total
 template <int KL, int KR, int KC>
 ft_status launch_rows(const ConvParams &p, int64_t planes, cudaStream_t s)
 {
-    constexpr int RB = 8;
+    // two leading taps hold twice the rows in registers: half the rows per warp
+    constexpr int RB = KL == 1 ? 8 : 4;
     const int64_t nstrips = ft::ceil_div(p.Mc, 128);
     const int64_t nrb = ft::ceil_div(p.Mr, RB);
-    const int64_t warps = planes * nstrips * nrb;
-    const int64_t blocks = ft::ceil_div(warps, kThreads / 32);
-    if (blocks > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
-    conv_rows_kernel<KL, KR, KC, RB><<<(unsigned)blocks, kThreads, 0, s>>>(p, nstrips, nrb, warps);
+    const int64_t wpp = nstrips * nrb;
+    const int64_t bx = ft::ceil_div(wpp, kThreads / 32);
+    const int64_t bz = ft::ceil_div(planes, 65535);
+    if (wpp > 0x7fffffffLL || bx > 0x7fffffffLL || bz > 65535) return FT_ERR_UNSUPPORTED;
+    const dim3 grid((unsigned)bx, (unsigned)std::min<int64_t>(planes, 65535), (unsigned)bz);
+    conv_rows_kernel<KL, KR, KC, RB><<<grid, kThreads, 0, s>>>(p, (int)nrb, (int)wpp, planes);
     return ft::check_launch();
 }
 
