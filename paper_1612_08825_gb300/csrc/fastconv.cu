@@ -391,9 +391,13 @@ conv_direct_kernel(const ConvParams p, int64_t total)
 // Grid: x = groups of 8 warps within a plane (a warp per strip x row block, row blocks
 // fastest), y and z = the output plane (z counts 65535 planes), so that a warp finds its
 // work with one 32-bit division and its input planes without any (lead_plane).
+// main_strips: strips of 128 columns done as above; when the output's last strip has
+// at most 4 columns it is not one of them: warps past main_strips * nrb take it with a
+// lane per output row (32 rows per warp), so that it costs 1/4 of a warp per 8 rows
+// instead of one (for example 257-column planes: 2 main strips and a 1-column tail).
 template <int KL, int KR, int KC, int RB>
 __global__ void __launch_bounds__(kThreads)
-conv_rows_kernel(const ConvParams p, int nrb, int warps_per_plane, int64_t planes)
+conv_rows_kernel(const ConvParams p, int nrb, int main_strips, int warps_per_plane, int64_t planes)
 {
     constexpr int NROW = RB + KR - 1;            // input rows per warp
     constexpr int WN = KC + 3;                   // window: KC - 1 halo + 4 own columns
@@ -401,15 +405,49 @@ conv_rows_kernel(const ConvParams p, int nrb, int warps_per_plane, int64_t plane
     const int wi = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     const int64_t plane = (int64_t)blockIdx.z * 65535 + blockIdx.y;
     if (wi >= warps_per_plane || plane >= planes) return;      // warp-uniform
-    const int strip = wi / nrb;
-    const int64_t m0 = (int64_t)(wi - strip * nrb) * RB;
-    const int64_t ox0 = (int64_t)strip * 128;
-    const int64_t c0 = ox0 + 4 * lane;
 
     // input plane of each leading kernel index (-1: outside the input)
     int64_t q[KL];
 #pragma unroll
     for (int R = 0; R < KL; ++R) q[R] = lead_plane(p, plane, R);
+
+    if (wi >= main_strips * nrb) {
+        // the narrow last strip: output row m, columns ox0 .. ox0 + w - 1 (w <= 4),
+        // terms in the order of the main path (R, kernel row a, kernel column b)
+        const int64_t m = (int64_t)(wi - main_strips * nrb) * 32 + lane;
+        if (m >= p.Mr) return;
+        const int64_t ox0 = (int64_t)main_strips * 128;
+        const int w = (int)(p.Mc - ox0);
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int R = 0; R < KL; ++R) {
+            if (q[R] < 0) continue;
+            const float *src = p.in + q[R] * p.Nr * p.Nc;
+#pragma unroll
+            for (int a = 0; a < KR; ++a) {
+                const int64_t gy = m - a;
+                if (gy < 0 || gy >= p.Nr) continue;
+#pragma unroll
+                for (int b = 0; b < KC; ++b) {
+                    const float kv = __ldg(p.ker + (R * KR + a) * KC + b);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int64_t gx = ox0 + c - b;
+                        if (c < w && gx >= 0 && gx < p.Nc) o[c] = fmaf(kv, __ldg(src + gy * p.Nc + gx), o[c]);
+                    }
+                }
+            }
+        }
+        float *orow = p.out + (plane * p.Mr + m) * p.Mc + ox0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < w) orow[c] = o[c];
+        return;
+    }
+    const int strip = wi / nrb;
+    const int64_t m0 = (int64_t)(wi - strip * nrb) * RB;
+    const int64_t ox0 = (int64_t)strip * 128;
+    const int64_t c0 = ox0 + 4 * lane;
     float kr[KL][KR][KC];
 #pragma unroll
     for (int R = 0; R < KL; ++R)
@@ -495,12 +533,14 @@ ft_status launch_rows(const ConvParams &p, int64_t planes, cudaStream_t s)
     constexpr int RB = KL == 1 ? 8 : 4;
     const int64_t nstrips = ft::ceil_div(p.Mc, 128);
     const int64_t nrb = ft::ceil_div(p.Mr, RB);
-    const int64_t wpp = nstrips * nrb;
+    const bool tail = nstrips > 1 && p.Mc - (nstrips - 1) * 128 <= 4;
+    const int64_t main_strips = tail ? nstrips - 1 : nstrips;
+    const int64_t wpp = main_strips * nrb + (tail ? ft::ceil_div(p.Mr, 32) : 0);
     const int64_t bx = ft::ceil_div(wpp, kThreads / 32);
     const int64_t bz = ft::ceil_div(planes, 65535);
     if (wpp > 0x7fffffffLL || bx > 0x7fffffffLL || bz > 65535) return FT_ERR_UNSUPPORTED;
     const dim3 grid((unsigned)bx, (unsigned)std::min<int64_t>(planes, 65535), (unsigned)bz);
-    conv_rows_kernel<KL, KR, KC, RB><<<grid, kThreads, 0, s>>>(p, (int)nrb, (int)wpp, planes);
+    conv_rows_kernel<KL, KR, KC, RB><<<grid, kThreads, 0, s>>>(p, (int)nrb, (int)main_strips, (int)wpp, planes);
     return ft::check_launch();
 }
 

@@ -54,6 +54,21 @@ def test_fastconv_small_shapes(shape, kshape):
     _check_full(E, k)
 
 
+@pytest.mark.parametrize("shape,kshape", [
+    ((37, 256), (2, 2)), ((45, 257), (3, 3)), ((20, 130), (1, 3)), ((70, 253), (2, 2)),
+    ((5, 33, 256), (2, 2, 2)), ((4, 19, 258), (2, 3, 3)), ((3, 70, 129), (2, 1, 2)),
+    ((6, 40, 126), (1, 3, 3)),
+])
+def test_fastconv_streaming_narrow_last_strip(shape, kshape):
+    """Outputs whose last 128-column strip has 1-4 columns (257, 259, 132, 254, 257, 260,
+    130, 128 + 0): that strip is taken with a lane per output row; planes with one or
+    two leading kernel taps, unaligned rows, pointer and image edges."""
+    E = scenes.normal_array(shape, seed=sum(shape) + 1)
+    k = scenes.normal_array(kshape, seed=200 + sum(kshape))
+    _check_full(E, k)
+    _check_full(E, k, offset=1)
+
+
 @pytest.mark.parametrize("kc", [5, 9, 17, 33, 65, 70])
 def test_fastconv_every_padding_bucket_and_direct_fallback(kc):
     E = scenes.uniform_array((20, 150), seed=kc)
