@@ -69,6 +69,18 @@ def test_fastconv_streaming_narrow_last_strip(shape, kshape):
     _check_full(E, k, offset=1)
 
 
+@pytest.mark.parametrize("shape,kshape", [
+    ((8, 40, 256), (5, 5, 5)), ((6, 70, 128), (1, 7, 7)), ((50, 1000), (15, 15)), ((4, 33, 264), (3, 4, 9)),
+    ((5, 36, 384), (1, 6, 17)), ((70, 252), (9, 5)),
+])
+def test_fastconv_copy_engine_narrow_last_tile(shape, kshape):
+    """FMA-bound kernels on the copy-engine path whose last 128-column output tile has few
+    columns inside the output (260, 134, 272, 400 columns; 1014 and 256 as controls)."""
+    E = scenes.normal_array(shape, seed=sum(shape) + 7)
+    k = scenes.normal_array(kshape, seed=300 + sum(kshape))
+    _check_full(E, k)
+
+
 @pytest.mark.parametrize("kc", [5, 9, 17, 33, 65, 70])
 def test_fastconv_every_padding_bucket_and_direct_fallback(kc):
     E = scenes.uniform_array((20, 150), seed=kc)
@@ -264,6 +276,7 @@ def _typed_input(shape, dtype, seed):
 @pytest.mark.parametrize("shape,kshape", [
     ((45, 640), (7, 5)), ((40, 640), (1, 9)), ((33, 320), (3, 17)), ((37, 531), (5, 5)),
     ((3, 24, 96), (2, 4, 3)), ((700,), (9,)), ((30, 64), (3, 40)), ((20, 96), (2, 2)),
+    ((3, 30, 256), (2, 5, 5)),               # copy-engine tiles, a 4-column last tile
 ])
 def test_fastconv_typed_inputs_match_oracle(dtype, shape, kshape):
     """uint8 / int16 / float16 / bfloat16 inputs, widened to FP32 exactly: the copy
