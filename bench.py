@@ -199,6 +199,23 @@ class L2Flush:
         self.torch.cuda._sleep(self.SPIN_CYCLES)
 
 
+def single_launch_us(dev, flush, fn, reps):
+    """Median device time of one call between CUDA events, L2 flushed before each."""
+    import torch
+    s = torch.cuda.current_stream(dev)
+    times = []
+    for _ in range(reps + 2):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        times.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    return float(np.median([a.elapsed_time(b) for a, b in times[2:]])) * 1e3
+
+
 def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
     import torch
     import paper_1612_08825_gb300 as ft
@@ -237,9 +254,18 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
         flops = 2.0 * nE * nk
         gbs = byts / t / 1e9
         bound = "fma" if flops / byts > fma_peak / (hbm_peak * 1e9) else "hbm"
-        rows.append({"input": list(shape), "kernel": list(kshape), "us": t * 1e6, "bound": bound,
-                     "GBps": gbs, "hbm_frac": gbs / hbm_peak, "GFLOPps": flops / t / 1e9,
-                     "fma_frac": flops / t / fma_peak, "algorithmic_bytes": byts, "flops": flops})
+        row = {"input": list(shape), "kernel": list(kshape), "us": t * 1e6, "bound": bound,
+               "GBps": gbs, "hbm_frac": gbs / hbm_peak, "GFLOPps": flops / t / 1e9,
+               "fma_frac": flops / t / fma_peak, "algorithmic_bytes": byts, "flops": flops}
+        if bound == "hbm":
+            # the same single-launch timing of a device copy of the same bytes (read the
+            # input, write as many bytes): what one launch of this size can reach here
+            dst = torch.empty(max(no, nE), dtype=torch.float32, device=dev)
+            row["copy_same_bytes_us"] = single_launch_us(
+                dev, flush, lambda: dst[:nE].copy_(E.reshape(-1)), reps) if no >= nE else None
+            if row["copy_same_bytes_us"]:
+                row["frac_of_copy"] = row["copy_same_bytes_us"] / row["us"]
+        rows.append(row)
     # inputs of other element types, staged by the copy engine in their own type and
     # widened in the kernel: bytes = input bytes + FP32 output
     for shape, kshape, dt in (((16, 1080, 1920), (1, 3, 3), torch.uint8), ((16, 1080, 1920), (1, 7, 7), torch.uint8),
@@ -341,6 +367,13 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
                      "algorithmic_bytes": byts, "direct_us": t_dir * 1e6, "speedup_vs_direct": t_dir / t_sep,
                      "direct_equivalent_GFLOPps": flops / t_sep / 1e9})
     del flush
+    # the device-side cost of one launch under this timing (a 1-element convolution)
+    one = torch.ones(1, device=dev)
+    o1 = ft.fastconv_nd(one, one)
+    rows.append({"single_launch_floor_us": single_launch_us(dev, flush, lambda: ft.fastconv_nd(one, one, out=o1),
+                                                            reps),
+                 "note": "a 1-element convolution timed like the rows above (L2 flush, device spin, "
+                         "events): the floor of any single launch"})
     return rows, launches
 
 

@@ -578,7 +578,7 @@ inline int64_t set_size(const PassParams &p)
 // ROWCHK / COLCHK: bounds checks on rows / element groups; MASK: cubes outside the
 // tile or the image are masked; SHIFT: edge tiles move inwards (padded images)
 template <typename Tin, typename Tout, bool WRITE, bool ROWCHK, bool COLCHK, bool MASK, bool SHIFT, int RPW>
-__global__ void __launch_bounds__(NT, FT_TTC_MINB)
+__global__ void __launch_bounds__(NT, RPW == 2 ? 3 : FT_TTC_MINB)
 ttc_pass_kernel(const PassParams p)
 {
     __shared__ float red[NSUM * NT];
@@ -661,7 +661,7 @@ cudaError_t launch(const PassParams &p, int npairs, cudaStream_t s, int *count)
 // of this tile class.  CHECK = false: interior tiles (vector loads, no masks);
 // CHECK = true: edge tiles (element checks, masks).
 template <typename Tin, typename Tout, bool WRITE, bool CHECK, int RPW>
-__global__ void __launch_bounds__(NT, FT_TTC_MINB)
+__global__ void __launch_bounds__(NT, RPW == 2 ? 3 : FT_TTC_MINB)
 ttc_batch_kernel(const PassParams *__restrict__ descs, const int *__restrict__ prefix, int npairs)
 {
     __shared__ float red[NSUM * NT];
