@@ -568,6 +568,10 @@ ttc_fused_kernel(const __grid_constant__ U units, int *status, int *counter, uns
     // thread 0's walk over its units (tickets in increasing order) and the items of each
     int u_pair = 0, u_tx = 0, u_next = 0, u_end = 0;
     bool done = false;          // the end marker has been issued
+    // the pair whose geometry each slot's descriptor holds, and the last pair whose maps
+    // this thread has fenced: consecutive items are mostly tiles of one strip, so the
+    // 192-byte copy and the fences are made only when the pair changes
+    int pair0 = -1, pair1 = -1, fenced = -1;
     auto issue_next = [&](int slot_b) -> bool {   // true: a copy is in flight for slot_b
         Item &it = info[slot_b];
         int kind = K_TILE, j = 0;
@@ -589,15 +593,21 @@ ttc_fused_kernel(const __grid_constant__ U units, int *status, int *counter, uns
             }
         }
         if (kind == K_TILE) j = u_next++;
-        geom_of(units, u_pair, it.g);
+        if ((slot_b ? pair1 : pair0) != u_pair) {
+            geom_of(units, u_pair, it.g);
+            if (slot_b) pair1 = u_pair;
+            else pair0 = u_pair;
+        }
         it.kind = kind;
         it.pair = u_pair;
         it.tx = u_tx;
         it.j = j;
         int z;
         const CUtensorMap *m = maps_of(units, u_pair, z);
-        if (GLOBAL_MAPS)
+        if (GLOBAL_MAPS && fenced != u_pair) {
             for (int k = 0; k < 4; ++k) ttc_tma::tensormap_acquire(m + k);
+            fenced = u_pair;
+        }
         unsigned char *buf = bufs + slot_b * BUF;
         const int x = u_tx * TC, y = kind == K_PRO ? j * TR - 16 : j * TR;
         // generic-proxy accesses of this buffer (earlier items) are ordered before the copies
