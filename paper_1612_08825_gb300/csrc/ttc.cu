@@ -27,7 +27,8 @@ namespace {
 
 using ttc_pass::NSUM;
 using ttc_merge::SolveDesc;
-using ttc_merge::merge_solve;
+using ttc_merge::merge_sums;
+using ttc_merge::solve_record;
 using ttc_pass::TR;
 using ttc_pass::TC;
 
@@ -47,24 +48,52 @@ struct SolveParams {
     int skip;                         // pairs [0, skip) are not written
 };
 
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(32 * ttc_merge::MERGE_ITEMS)
 ttc_solve_kernel(const SolveParams p)
 {
-    const int item = blockIdx.x;                 // pair * levels + level
-    const int pair = item / p.levels, l = item - pair * p.levels;
-    if (pair < p.skip) return;
-    const int ntiles = p.ntiles[l];
-    merge_solve(p.partials + p.poff[l] + (int64_t)pair * ntiles * NSUM, ntiles, l, p.inv_scale[l], p.ncubes[l],
-                p.mode, p.status, p.out + item);
+    __shared__ double ssum[ttc_merge::MERGE_ITEMS][NSUM];
+    const int MI = blockDim.x >> 5;                           // items of this CTA
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = p.npairs * p.levels;
+    const int item = blockIdx.x * MI + warp;                  // pair * levels + level
+    if (item < total) {
+        const int pair = item / p.levels, l = item - pair * p.levels;
+        if (pair >= p.skip) {
+            double acc[NSUM];
+            merge_sums(p.partials + p.poff[l] + (int64_t)pair * p.ntiles[l] * NSUM, p.ntiles[l], acc);
+            if (lane == 0)
+                for (int s = 0; s < NSUM; ++s) ssum[warp][s] = acc[s];
+        }
+    }
+    __syncthreads();
+    const int it = blockIdx.x * MI + lane;
+    if (warp == 0 && lane < MI && it < total) {
+        const int pair = it / p.levels, l = it - pair * p.levels;
+        if (pair >= p.skip) solve_record(ssum[lane], l, p.inv_scale[l], p.ncubes[l], p.mode, p.status, p.out + it);
+    }
 }
 
-__global__ void __launch_bounds__(32)
-ttc_batch_solve_kernel(const float *partials, const SolveDesc *sd, int mode, const int *status,
+__global__ void __launch_bounds__(32 * ttc_merge::MERGE_ITEMS)
+ttc_batch_solve_kernel(const float *partials, const SolveDesc *sd, int total, int mode, const int *status,
                        ttc_level_result *out)
 {
-    const SolveDesc d = sd[blockIdx.x];          // blockIdx.x = pair * levels + level
-    merge_solve(partials + d.poff, d.ntiles, d.level, ldexp(1.0, -4 - 4 * d.level - d.shift), d.ncubes, mode, status,
-                out + blockIdx.x);
+    __shared__ double ssum[ttc_merge::MERGE_ITEMS][NSUM];
+    const int MI = blockDim.x >> 5;                           // items of this CTA
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * MI + warp;                  // pair * levels + level
+    if (item < total) {
+        const SolveDesc d = sd[item];
+        double acc[NSUM];
+        merge_sums(partials + d.poff, d.ntiles, acc);
+        if (lane == 0)
+            for (int s = 0; s < NSUM; ++s) ssum[warp][s] = acc[s];
+    }
+    __syncthreads();
+    const int it = blockIdx.x * MI + lane;
+    if (warp == 0 && lane < MI && it < total) {
+        const SolveDesc d = sd[it];
+        solve_record(ssum[lane], d.level, ldexp(1.0, -4 - 4 * d.level - d.shift), d.ncubes, mode, status, out + it);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -629,6 +658,13 @@ int sm_count()
     return std::max(nsm, 1);
 }
 
+// (pair, level) items per CTA of the merge kernels: enough to spread them over every SM
+// (the FP64 merges of one SM run one after another), at most MERGE_ITEMS
+int merge_items_per_cta(int items)
+{
+    return (int)std::min<int64_t>(ttc_merge::MERGE_ITEMS, std::max<int64_t>(1, ft::ceil_div(items, sm_count())));
+}
+
 // Tiles per unit of the all-levels kernel: whole strips when there are at least four
 // units per CTA of the grid, else shorter runs (each below the top of its strip starts
 // with a prologue).
@@ -827,7 +863,9 @@ ft_status launch_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStream
     sp.status = ctx->status;
     sp.out = out;
     sp.skip = skip;
-    ttc_solve_kernel<<<(unsigned)(g.npairs * g.levels), 32, 0, s>>>(sp);
+    const int items = g.npairs * g.levels;
+    const int mi = merge_items_per_cta(items);
+    ttc_solve_kernel<<<(unsigned)ft::ceil_div(items, mi), 32 * mi, 0, s>>>(sp);
     return ft::check_launch();
 }
 
@@ -1196,8 +1234,9 @@ ft_status batch_run_impl(ttc_ctx *ctx, int mode, ttc_level_result *out, cudaStre
         else e = batch_level<float>(ctx, l, &count, s);
     }
     if (e == cudaSuccess) {
-        ttc_batch_solve_kernel<<<(unsigned)(b.npairs * b.levels), 32, 0, s>>>(ctx->partials, ctx->d_sdesc, mode,
-                                                                              ctx->status, out);
+        const int items = b.npairs * b.levels, mi = merge_items_per_cta(items);
+        ttc_batch_solve_kernel<<<(unsigned)ft::ceil_div(items, mi), 32 * mi, 0, s>>>(ctx->partials, ctx->d_sdesc,
+                                                                                     items, mode, ctx->status, out);
         e = cudaGetLastError();
         ++count;
     }

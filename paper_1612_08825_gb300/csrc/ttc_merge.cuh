@@ -88,13 +88,11 @@ __device__ void solve_one(const double s[NSUM], int mode, int level, ttc_level_r
     r->resid = s[9] > 0.0 ? res / s[9] : 0.0;
 }
 
-// One warp: FP64 merge of ntiles FP32 tile partials in a fixed order (lane-strided,
-// then a shuffle tree), scaling to level-l mean-image units, solve; lane 0 writes.
-__device__ __forceinline__ void merge_solve(const float *src, int ntiles, int l, double inv_scale, int64_t ncubes,
-                                            int mode, const int *status, ttc_level_result *out)
+// One warp: FP64 merge of ntiles FP32 tile partials in a fixed order (lane-strided, then
+// a shuffle tree); every lane ends with the ten totals.
+__device__ __forceinline__ void merge_sums(const float *src, int ntiles, double acc[NSUM])
 {
     const int lane = threadIdx.x & 31;
-    double acc[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) acc[s] = 0.0;
     for (int t = lane; t < ntiles; t += 32)
@@ -104,17 +102,27 @@ __device__ __forceinline__ void merge_solve(const float *src, int ntiles, int l,
     for (int o = 16; o >= 1; o >>= 1)
 #pragma unroll
         for (int s = 0; s < NSUM; ++s) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
-    if (lane == 0) {
-        ttc_level_result r;
-        for (int s = 0; s < NSUM; ++s) r.sums[s] = acc[s] * inv_scale;
-        r.n = ncubes;
-        solve_one(r.sums, mode, l, &r);
-        // status word: bit 0 a wait gave up, bit 1 a checked build found an access out of bounds
-        const int st = *status;
-        if (st & 1) r.flags |= FT_FLAG_TIMEOUT;
-        if (st & 2) r.flags |= FT_FLAG_BOUNDS;
-        *out = r;
-    }
 }
+
+// One thread: the merged sums scaled to level-l mean-image units, the solve, the status
+// flags, the record.
+__device__ __forceinline__ void solve_record(const double *acc, int l, double inv_scale, int64_t ncubes, int mode,
+                                             const int *status, ttc_level_result *out)
+{
+    ttc_level_result r;
+    for (int s = 0; s < NSUM; ++s) r.sums[s] = acc[s] * inv_scale;
+    r.n = ncubes;
+    solve_one(r.sums, mode, l, &r);
+    // status word: bit 0 a wait gave up, bit 1 a checked build found an access out of bounds
+    const int st = *status;
+    if (st & 1) r.flags |= FT_FLAG_TIMEOUT;
+    if (st & 2) r.flags |= FT_FLAG_BOUNDS;
+    *out = r;
+}
+
+// Most (pair, level) items per CTA of the merge kernels: a warp merges each, then the
+// lanes of the first warp solve them side by side (FP64 runs at a small fraction of the
+// FP32 rate on this part, so a solve gets one lane, not a warp)
+constexpr int MERGE_ITEMS = 16;
 
 }  // namespace ttc_merge
