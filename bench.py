@@ -366,7 +366,6 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
                      "bound": "hbm", "GBps": byts / t_sep / 1e9, "hbm_frac": byts / t_sep / 1e9 / hbm_peak,
                      "algorithmic_bytes": byts, "direct_us": t_dir * 1e6, "speedup_vs_direct": t_dir / t_sep,
                      "direct_equivalent_GFLOPps": flops / t_sep / 1e9})
-    del flush
     # the device-side cost of one launch under this timing (a 1-element convolution)
     one = torch.ones(1, device=dev)
     o1 = ft.fastconv_nd(one, one)
@@ -374,6 +373,7 @@ def fastconv_sweep(dev, hbm_peak, fma_peak, reps):
                                                             reps),
                  "note": "a 1-element convolution timed like the rows above (L2 flush, device spin, "
                          "events): the floor of any single launch"})
+    del flush
     return rows, launches
 
 
