@@ -5,7 +5,7 @@
 // Every admitted stream owns three device frame slots and two pyramid blocks (levels
 // 1..L-1 of its last two frames).  A tick takes at most one waiting frame per stream
 // (oldest arrival first, at most max_batch pairs), uploads the frames on a copy stream
-// (one 2-D copy each, from the caller's host memory), and runs one ttc_batch_prepare +
+// (one copy each, from the caller's host memory), and runs one ttc_batch_prepare +
 // ttc_batch_run on the compute stream: the pair (previous frame, new frame) reads the
 // previous frame's pyramid from one block and writes the new frame's to the other, so
 // every frame is uploaded once and its pyramid built once.  The records come back to
@@ -158,7 +158,7 @@ ft_status launch_tick(ttc_server *s)
         st.pending.pop_front();
         npairs += pair;
     }
-    // uploads: one 2-D copy per frame into the slot after the resident one
+    // uploads: one copy per frame into the slot after the resident one
     cudaError_t e = cudaSuccess;
     s->descs.clear();
     for (Item &it : t.items) {
@@ -166,8 +166,13 @@ ft_status launch_tick(ttc_server *s)
         const int slot = (st.cur + 1) % 3;
         unsigned char *dst = st.mem + (size_t)slot * st.slot_bytes;
         const size_t row = (size_t)st.W * (size_t)s->es;
-        e = cudaMemcpy2DAsync(dst, row, it.f.host, (size_t)it.f.pitch, row, (size_t)st.H, cudaMemcpyHostToDevice,
-                              s->copy);
+        // contiguous rows: one linear copy (a 2-D copy of many short rows runs well below the
+        // link's rate); otherwise a 2-D copy
+        if ((size_t)it.f.pitch == row)
+            e = cudaMemcpyAsync(dst, it.f.host, row * (size_t)st.H, cudaMemcpyHostToDevice, s->copy);
+        else
+            e = cudaMemcpy2DAsync(dst, row, it.f.host, (size_t)it.f.pitch, row, (size_t)st.H,
+                                  cudaMemcpyHostToDevice, s->copy);
         if (e != cudaSuccess) return cuda_fail(e);
         if (st.cur >= 0) {
             unsigned char *pyr = st.mem + 3 * st.slot_bytes;

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -363,6 +364,31 @@ float centre_off(int n, int l)
 
 }  // namespace
 
+namespace {
+
+// key of a batch frame's tensor map: the map is a function of these values only
+struct MapKey {
+    const void *base;
+    int W, H, bw;
+    int64_t pitch;
+    bool operator==(const MapKey &o) const
+    {
+        return base == o.base && W == o.W && H == o.H && bw == o.bw && pitch == o.pitch;
+    }
+};
+struct MapKeyHash {
+    size_t operator()(const MapKey &k) const
+    {
+        size_t h = std::hash<const void *>()(k.base);
+        h = h * 1000003u ^ (size_t)k.W;
+        h = h * 1000003u ^ (size_t)k.H;
+        h = h * 1000003u ^ (size_t)k.bw;
+        return h * 1000003u ^ (size_t)k.pitch;
+    }
+};
+
+}  // namespace
+
 struct ttc_ctx {
     int max_H, max_W, max_levels, max_pairs;
     float *partials;
@@ -385,10 +411,15 @@ struct ttc_ctx {
     int4 *d_units;                    // [items_cap]: its units (pair, strip, first tile row, tiles)
     size_t items_cap;
     size_t off_maps, off_items, off_geoms, off_units;   // byte offsets of those arrays in the staging buffers
-    unsigned char *h_stage;           // pinned staging buffer of the arrays
+    unsigned char *h_stage;           // pinned staging buffer of the arrays: the half in use
+    unsigned char *h_stage_buf[2];    // two halves, used alternately by prepares
     size_t stage_bytes;
-    cudaEvent_t stage_ev;             // the last upload from h_stage
-    bool stage_pending;
+    cudaEvent_t stage_ev_buf[2];      // the last upload from each half
+    bool stage_pending_buf[2];
+    int stage_idx;                    // the half the next prepare fills
+    // tensor maps of batch frames, by (base, W, H, pitch, box width): a serving loop's frames
+    // live in a few fixed slots, so most prepares find their maps here instead of encoding them
+    std::unordered_map<MapKey, CUtensorMap, MapKeyHash> map_cache;
     struct {
         int npairs, levels, dtype;
         int rpw[FT_MAX_LEVELS], in_es[FT_MAX_LEVELS], out_es[FT_MAX_LEVELS];
@@ -475,13 +506,19 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     c->stage_bytes = c->off_units + c->items_cap * sizeof(int4);
     unsigned char *dbuf = nullptr;
     e = cudaMalloc(&dbuf, c->stage_bytes);
-    if (e == cudaSuccess) e = cudaHostAlloc(&c->h_stage, c->stage_bytes, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaHostAlloc(&c->h_stage_buf[k], c->stage_bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev_buf[k], cudaEventDisableTiming);
+    }
+    c->h_stage = c->h_stage_buf[0];
     c->h_pairs = new (std::nothrow) ttc_pair_desc[max_pairs];
     if (e != cudaSuccess || !c->h_pairs) {
         ft::set_cuda_error(e != cudaSuccess ? e : cudaErrorMemoryAllocation);
         cudaFree(dbuf);
-        if (c->h_stage) cudaFreeHost(c->h_stage);
+        for (int k = 0; k < 2; ++k) {
+            if (c->h_stage_buf[k]) cudaFreeHost(c->h_stage_buf[k]);
+            if (c->stage_ev_buf[k]) cudaEventDestroy(c->stage_ev_buf[k]);
+        }
         delete[] c->h_pairs;
         cudaFree(part);
         cudaFree(img);
@@ -519,12 +556,15 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
 extern "C" void ttc_ctx_destroy(ttc_ctx *ctx)
 {
     if (!ctx) return;
-    if (ctx->stage_pending) cudaEventSynchronize(ctx->stage_ev);
+    for (int k = 0; k < 2; ++k)
+        if (ctx->stage_pending_buf[k]) cudaEventSynchronize(ctx->stage_ev_buf[k]);
     cudaFree(ctx->partials);
     cudaFree(ctx->images);
     cudaFree(ctx->d_descs);
-    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-    if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->h_stage_buf[k]) cudaFreeHost(ctx->h_stage_buf[k]);
+        if (ctx->stage_ev_buf[k]) cudaEventDestroy(ctx->stage_ev_buf[k]);
+    }
     if (ctx->ring_used) cudaEventSynchronize(ctx->ev_ring_done);
     for (int b = 0; b < 2; ++b) {
         if (ctx->cstream[b]) {
@@ -570,6 +610,22 @@ bool u8_frame_map(CUtensorMap *m, const void *base, int W, int H, int npairs, in
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the tensor map of one batch frame (one pair coordinate), from the context's cache or
+// encoded and cached
+bool batch_frame_map(ttc_ctx *ctx, CUtensorMap *m, const void *base, int W, int H, int64_t pitch, int bw)
+{
+    const MapKey k{base, W, H, bw, pitch};
+    const auto it = ctx->map_cache.find(k);
+    if (it != ctx->map_cache.end()) {
+        *m = it->second;
+        return true;
+    }
+    if (!u8_frame_map(m, base, W, H, 1, pitch, (pitch * H + 15) / 16 * 16, bw)) return false;
+    if (ctx->map_cache.size() >= 4096) ctx->map_cache.clear();
+    ctx->map_cache.emplace(k, *m);
+    return true;
 }
 
 // the persistent TMA level-0 kernel over a set of work items: two CTAs per SM
@@ -952,13 +1008,17 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
         rpw[l] = t64 < 1216 ? 2 : 8;
     }
     const size_t nd = (size_t)ctx->max_levels * ctx->max_pairs;
-    if (ctx->stage_pending) {
-        cudaError_t e = cudaEventSynchronize(ctx->stage_ev);
+    // the half of the staging buffer this prepare fills: free once its last upload (two
+    // prepares ago) has run
+    const int si = ctx->stage_idx;
+    ctx->h_stage = ctx->h_stage_buf[si];
+    if (ctx->stage_pending_buf[si]) {
+        cudaError_t e = cudaEventSynchronize(ctx->stage_ev_buf[si]);
         if (e != cudaSuccess) {
             ft::set_cuda_error(e);
             return FT_ERR_CUDA;
         }
-        ctx->stage_pending = false;
+        ctx->stage_pending_buf[si] = false;
     }
     // level 0 of uint8 pairs whose frames the copy engine can address (16-byte aligned
     // frames and pitch) runs the persistent TMA kernel when the plan has 64-row tiles
@@ -1014,11 +1074,10 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
         const bool aligned16 = (reinterpret_cast<uintptr_t>(d.prev) & 15) == 0 &&
                                (reinterpret_cast<uintptr_t>(d.cur) & 15) == 0 && (d.pitch_bytes & 15) == 0;
         if (fused_dt && aligned16) {
-            const int64_t ps = (d.pitch_bytes * d.H + 15) / 16 * 16;
-            bool ok = u8_frame_map(&hmaps[4 * p + 0], d.prev, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::BW) &&
-                      u8_frame_map(&hmaps[4 * p + 1], d.cur, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::BW) &&
-                      u8_frame_map(&hmaps[4 * p + 2], d.prev, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::XW) &&
-                      u8_frame_map(&hmaps[4 * p + 3], d.cur, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::XW);
+            bool ok = batch_frame_map(ctx, &hmaps[4 * p + 0], d.prev, d.W, d.H, d.pitch_bytes, ttc_tma::BW) &&
+                      batch_frame_map(ctx, &hmaps[4 * p + 1], d.cur, d.W, d.H, d.pitch_bytes, ttc_tma::BW) &&
+                      batch_frame_map(ctx, &hmaps[4 * p + 2], d.prev, d.W, d.H, d.pitch_bytes, ttc_tma::XW) &&
+                      batch_frame_map(ctx, &hmaps[4 * p + 3], d.cur, d.W, d.H, d.pitch_bytes, ttc_tma::XW);
             if (ok) {
                 Geometry gf;
                 geometry_fused(d.H, d.W, levels, 1, gf);
@@ -1058,11 +1117,10 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
         }
         bool tma = tma_level0 && aligned16;
         if (tma) {
-            const int64_t ps = (d.pitch_bytes * d.H + 15) / 16 * 16;
-            tma = u8_frame_map(&hmaps[4 * p + 0], d.prev, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::BW) &&
-                  u8_frame_map(&hmaps[4 * p + 1], d.cur, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::BW) &&
-                  u8_frame_map(&hmaps[4 * p + 2], d.prev, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::XW) &&
-                  u8_frame_map(&hmaps[4 * p + 3], d.cur, d.W, d.H, 1, d.pitch_bytes, ps, ttc_tma::XW);
+            tma = batch_frame_map(ctx, &hmaps[4 * p + 0], d.prev, d.W, d.H, d.pitch_bytes, ttc_tma::BW) &&
+                  batch_frame_map(ctx, &hmaps[4 * p + 1], d.cur, d.W, d.H, d.pitch_bytes, ttc_tma::BW) &&
+                  batch_frame_map(ctx, &hmaps[4 * p + 2], d.prev, d.W, d.H, d.pitch_bytes, ttc_tma::XW) &&
+                  batch_frame_map(ctx, &hmaps[4 * p + 3], d.cur, d.W, d.H, d.pitch_bytes, ttc_tma::XW);
         }
         const uintptr_t al = dtype == FT_U8 ? 3 : 15;
         const int vec0 = ((reinterpret_cast<uintptr_t>(d.prev) & al) == 0 &&
@@ -1168,12 +1226,13 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
     if (e == cudaSuccess && n_units > 0)
         e = cudaMemcpyAsync(dstage + ctx->off_units, ctx->h_stage + ctx->off_units, (size_t)n_units * sizeof(int4),
                             cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev_buf[si], s);
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
         return FT_ERR_CUDA;
     }
-    ctx->stage_pending = true;
+    ctx->stage_pending_buf[si] = true;
+    ctx->stage_idx = si ^ 1;
     if (pairs != ctx->h_pairs)
         for (int p = 0; p < npairs; ++p) ctx->h_pairs[p] = pairs[p];
     ctx->b.npairs = npairs;
