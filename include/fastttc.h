@@ -526,10 +526,13 @@ ft_status ttc_server_step(ttc_server *srv, int wait, ttc_served *done, int max_d
  * each of the nstreams admitted streams `ids` supplied with a waiting frame, taken in turn
  * from its nframes host frames (frames[i * nframes + k], row pitch pitches[i]; page-locked
  * memory lets the uploads run asynchronously), and steps the server until `pairs` results
- * (FT_SERVED_RESULT) have come back.  Every tick then carries one pair per stream, so the
- * rate is set by the runtime and the device rather than by the caller.  Reports are
- * consumed; *seconds (wall clock), *served, *p50_ms and *p99_ms (submission to report)
- * are written when non-null.  Errors: FT_ERR_INVALID_ARG, and those of submit and step.
+ * (FT_SERVED_RESULT) have come back, keeping two ticks in flight (the next tick's uploads
+ * overlap the kernels of the one being waited for).  Every tick then carries one pair per
+ * stream, so the rate is set by the runtime and the device rather than by the caller.  The
+ * ticks still in flight at the end complete before the call returns (their pairs count,
+ * so *served may exceed `pairs`) and the server is idle again.  Reports are consumed;
+ * *seconds (wall clock), *served, *p50_ms and *p99_ms (submission to report) are written
+ * when non-null.  Errors: FT_ERR_INVALID_ARG, and those of submit and step.
  */
 ft_status ttc_server_drive(ttc_server *srv, const int *ids, int nstreams, const void *const *frames,
                            const int64_t *pitches, int nframes, int64_t pairs, double *seconds, int64_t *served,

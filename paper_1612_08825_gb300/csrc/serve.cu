@@ -416,6 +416,17 @@ extern "C" ft_status ttc_server_drive(ttc_server *s, const int *ids, int nstream
     lat.reserve((size_t)pairs);
     std::vector<ttc_served> done((size_t)std::max(64, 2 * nstreams));
     int64_t got = 0;
+    auto step = [&](int wait) {
+        int n = 0;
+        const ft_status st = ttc_server_step(s, wait, done.data(), (int)done.size(), &n);
+        const double t = now();
+        for (int k = 0; k < n; ++k)
+            if (done[(size_t)k].status == FT_SERVED_RESULT) {
+                lat.push_back(1e3 * (t - done[(size_t)k].t_arrival));
+                ++got;
+            }
+        return st;
+    };
     while (got < pairs) {
         for (int i = 0; i < nstreams; ++i) {
             if (ttc_server_waiting(s, ids[i]) > 0) continue;
@@ -424,15 +435,19 @@ extern "C" ft_status ttc_server_drive(ttc_server *s, const int *ids, int nstream
                                                    pitches[i], q, now());
             if (st != FT_OK) return st;
         }
-        int n = 0;
-        const ft_status st = ttc_server_step(s, 1, done.data(), (int)done.size(), &n);
+        // wait only when a tick is already in flight: this step launches a second one first,
+        // so the next tick's host work and uploads overlap the kernels of the one waited for
+        const ft_status st = step(ttc_server_in_flight(s) >= 1 ? 1 : 0);
         if (st != FT_OK) return st;
-        const double t = now();
-        for (int k = 0; k < n; ++k)
-            if (done[(size_t)k].status == FT_SERVED_RESULT) {
-                lat.push_back(1e3 * (t - done[(size_t)k].t_arrival));
-                ++got;
-            }
+    }
+    // the ticks still in flight complete (their pairs count) before the call returns, so
+    // the server is idle again
+    for (;;) {
+        bool waiting = false;
+        for (int i = 0; i < nstreams; ++i) waiting = waiting || ttc_server_waiting(s, ids[i]) > 0;
+        if (!waiting && ttc_server_in_flight(s) == 0) break;
+        const ft_status st = step(1);
+        if (st != FT_OK) return st;
     }
     if (seconds) *seconds = now();
     if (served) *served = got;

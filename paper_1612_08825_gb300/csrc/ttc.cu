@@ -507,7 +507,7 @@ extern "C" ft_status ttc_ctx_create(ttc_ctx **ctx, int max_H, int max_W, int max
     unsigned char *dbuf = nullptr;
     e = cudaMalloc(&dbuf, c->stage_bytes);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaHostAlloc(&c->h_stage_buf[k], c->stage_bytes, cudaHostAllocDefault);
+        e = cudaHostAlloc(&c->h_stage_buf[k], c->stage_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev_buf[k], cudaEventDisableTiming);
     }
     c->h_stage = c->h_stage_buf[0];
@@ -976,6 +976,30 @@ extern "C" ft_status ttc_solve(ttc_ctx *ctx, const void *prev, const void *cur, 
 
 namespace {
 
+// Ranges of the staging buffer a prepare uploads, in 16-byte words.
+struct StageRanges {
+    const int4 *src[5];         // pinned host staging (addressable from kernels under unified addressing)
+    int4 *dst[5];               // device staging
+    long long start[6];         // word prefix over the ranges
+    int nr;
+};
+
+// Copies the staged arrays of a prepare from pinned host memory to the device staging
+// buffer.  A kernel rather than copy-engine copies: a small copy on the compute stream
+// would otherwise queue behind the frame uploads that another stream has pending on the
+// same copy engine (a serving loop's next tick), delaying the kernels that read it.
+__global__ void __launch_bounds__(256) stage_copy_kernel(const StageRanges r)
+{
+    const long long total = r.start[r.nr];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < r.nr && i >= r.start[k + 1]) ++k;
+        const long long w = i - r.start[k];
+        r.dst[k][w] = r.src[k][w];
+    }
+}
+
 ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npairs, int dtype, int levels,
                              cudaStream_t s)
 {
@@ -1212,20 +1236,26 @@ ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npair
     for (int l = 0; l < levels; ++l)
         if (n_int[l] > 0x7fffffffLL || n_edge[l] > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
     if (n_tma > 0x7fffffffLL) return FT_ERR_UNSUPPORTED;
+    // one kernel uploads the used parts of the staging buffer (every part starts on a
+    // 128-byte boundary; sizes rounded up to 16 bytes stay inside their part)
     unsigned char *dstage = reinterpret_cast<unsigned char *>(ctx->d_descs);
-    cudaError_t e = cudaMemcpyAsync(dstage, ctx->h_stage, ctx->off_maps, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && (n_tma > 0 || n_units > 0))
-        e = cudaMemcpyAsync(dstage + ctx->off_maps, ctx->h_stage + ctx->off_maps,
-                            (size_t)npairs * 4 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n_tma > 0)
-        e = cudaMemcpyAsync(dstage + ctx->off_items, ctx->h_stage + ctx->off_items, (size_t)n_tma * sizeof(int2),
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n_units > 0)
-        e = cudaMemcpyAsync(dstage + ctx->off_geoms, ctx->h_stage + ctx->off_geoms,
-                            (size_t)npairs * sizeof(ttc_fused::Geom), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n_units > 0)
-        e = cudaMemcpyAsync(dstage + ctx->off_units, ctx->h_stage + ctx->off_units, (size_t)n_units * sizeof(int4),
-                            cudaMemcpyHostToDevice, s);
+    StageRanges r{};
+    auto add = [&](size_t off, size_t bytes) {
+        if (bytes == 0) return;
+        r.src[r.nr] = reinterpret_cast<const int4 *>(ctx->h_stage + off);
+        r.dst[r.nr] = reinterpret_cast<int4 *>(dstage + off);
+        r.start[r.nr + 1] = r.start[r.nr] + (long long)((bytes + 15) / 16);
+        ++r.nr;
+    };
+    add(0, ctx->off_maps);
+    if (n_tma > 0 || n_units > 0) add(ctx->off_maps, (size_t)npairs * 4 * sizeof(CUtensorMap));
+    if (n_tma > 0) add(ctx->off_items, (size_t)n_tma * sizeof(int2));
+    if (n_units > 0) add(ctx->off_geoms, (size_t)npairs * sizeof(ttc_fused::Geom));
+    if (n_units > 0) add(ctx->off_units, (size_t)n_units * sizeof(int4));
+    const long long words = r.start[r.nr];
+    const int grid = (int)std::min<long long>(std::max<long long>(1, (words + 255) / 256), 2LL * sm_count());
+    stage_copy_kernel<<<grid, 256, 0, s>>>(r);
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev_buf[si], s);
     if (e != cudaSuccess) {
         ft::set_cuda_error(e);
