@@ -276,3 +276,61 @@ def test_native_load_generator():
     for c in res:
         assert c.records.shape[0] == LEVELS and np.all(c.records["flags"] & ft.FLAG_TIMEOUT == 0)
     srv.close()
+
+
+def _serve_native_records(streams, frames, dtype):
+    srv = NativeServer(1080, 1920, LEVELS, 40 << 30, max_batch=8, rows_per_tile=PLAN, dtype=dtype)
+    for sid, H, W in streams:
+        assert srv.admit(sid, H, W)
+    done = []
+    for k in range(NFR):
+        for sid, _, _ in streams:
+            assert srv.offer(Frame(sid, k, float(k), frames[sid][k]))
+        done += srv.step()
+    done += srv.drain()
+    n = srv.stats["results"]
+    srv.close()
+    return {(c.stream, c.seq): (c.records.tobytes(), c.level) for c in done if c.records is not None}, n
+
+
+def test_native_server_upload_paths_bitwise():
+    """A frame reaches its device slot by the gather kernel (under 1 MB, in page-locked
+    memory, rows and pitch whole 16-byte words) or by the copy engine (pageable memory,
+    large frames, other pitches); contiguous or pitched, the records are bitwise the same."""
+    streams = [(0, 120, 160), (1, 240, 320), (2, 480, 640), (3, 720, 1280), (4, 100, 200), (5, 1080, 1920)]
+    for dtype in (torch.uint8, torch.float32):
+        ss = streams if dtype == torch.uint8 else streams[:3]
+        base = {sid: _video(H, W, NFR, 1300 + sid) for sid, H, W in ss}
+        if dtype != torch.uint8:
+            base = {sid: v.float() for sid, v in base.items()}
+        es = base[0].element_size()
+
+        def pitched(v, pin, extra):
+            n, H, W = v.shape
+            buf = torch.zeros((n, H, W + extra), dtype=v.dtype)
+            if pin:
+                buf = buf.pin_memory()
+            buf[:, :, :W] = v
+            return buf[:, :, :W]
+
+        def pad16(W):
+            # elements that take the row to the next multiple of 16 bytes, plus 16 bytes
+            return (-(W * es) % 16) // es + 16 // es
+
+        variants = {
+            "page-locked": {sid: v.pin_memory() for sid, v in base.items()},
+            "pageable": {sid: v.clone() for sid, v in base.items()},
+            "page-locked pitched": {sid: pitched(v, True, pad16(v.shape[2])) for sid, v in base.items()},
+            "pageable pitched": {sid: pitched(v, False, pad16(v.shape[2])) for sid, v in base.items()},
+            "page-locked, pitch not a 16-byte multiple": {sid: pitched(v, True, 3) for sid, v in base.items()},
+        }
+        ref = None
+        for name, frames in variants.items():
+            got, n = _serve_native_records(ss, frames, dtype)
+            assert n == len(ss) * (NFR - 1), name
+            if ref is None:
+                ref = got
+            else:
+                assert got.keys() == ref.keys(), name
+                for key in ref:
+                    assert got[key] == ref[key], (dtype, name, key)
