@@ -39,6 +39,7 @@ import argparse
 import json
 import math
 import os
+import statistics
 import subprocess
 import sys
 import time
@@ -568,6 +569,24 @@ def batch_oracle_errors(pairs, res, levels):
             "per_pair_max_sum_err": [float(f"{e:.3g}") for e in per_pair]}
 
 
+def h2d_link_gbs(dev, nbytes, reps=5):
+    """Host-to-device rate of one copy of nbytes from page-locked memory (median of reps)."""
+    import torch
+    src = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    dst = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    ts = []
+    for _ in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    return nbytes / statistics.median(ts[1:]) / 1e9
+
+
 def serve_bench(dev, args):
     """Serving: 64 camera streams (16 each of 320x240, 640x480, 1280x720, 1920x1080),
     uint8, 4 levels, FOE; Poisson arrivals at 30 fps per stream replayed in real time
@@ -636,9 +655,16 @@ def serve_bench(dev, args):
             # (no Python per frame), so the rate is the runtime's and the device's
             drv = srv.drive({sid: list(frames[sid]) for sid, *_ in specs}, pairs=200 * len(specs))
             px = sum(H * W for _, H, W, *_ in specs) / len(specs)
+            # every pair uploads one new frame: the upload rate against one host-to-device
+            # copy of a tick's bytes from page-locked memory (the host link's rate)
+            tick_bytes = sum(frames[sid][0].numel() * frames[sid][0].element_size() for sid, *_ in specs)
+            link = h2d_link_gbs(dev, tick_bytes)
+            up = drv["pairs"] / drv["seconds"] * tick_bytes / len(specs) / 1e9
             res["driven"] = {"pairs_per_s": drv["pairs"] / drv["seconds"], "p50_ms": drv["p50_ms"],
                              "p99_ms": drv["p99_ms"], "pairs": drv["pairs"],
                              "gpx_per_s": drv["pairs"] / drv["seconds"] * px / 1e9,
+                             "upload_bytes_per_tick": tick_bytes, "upload_gbs": up, "h2d_copy_gbs": link,
+                             "frac_of_h2d_copy": up / link,
                              "driver": "ttc_server_drive (native loop, one waiting frame per stream)"}
             srv.close()
         del srv, eng
