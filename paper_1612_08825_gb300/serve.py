@@ -573,8 +573,10 @@ class NativeServer:
     def drive(self, frames: Dict[int, list], pairs: int) -> dict:
         """The library's load generator (ttc_server_drive): every stream in `frames`
         (sid -> list of host frames of its size, cycled) always has a frame waiting; the
-        server is stepped natively until `pairs` results are back.  Returns seconds,
-        pairs served and p50 / p99 latency (ms, submission to report)."""
+        server is stepped natively, two ticks in flight, until `pairs` results are back,
+        and the ticks still in flight then complete too (so "pairs" may exceed the
+        request; the server is idle on return).  Returns seconds, pairs served and
+        p50 / p99 latency (ms, submission to report)."""
         ct = self._ct
         sids = list(frames)
         nf = len(frames[sids[0]])
