@@ -398,7 +398,9 @@ ft_status ttc_reduce_solve(ttc_ctx *ctx, int mode, ttc_level_result *out, void *
  * descriptors; the frames are device memory owned by the caller and must stay valid
  * and unchanged in address until the last ttc_batch_run that uses them), checks them,
  * lays out the context workspace, and uploads a work list and per-pair descriptors on
- * `stream`.  ttc_batch_run then performs, for every pair and level, the same
+ * `stream` (one small kernel that reads them from the context's page-locked staging
+ * memory, which has two halves: a prepare waits on the host only for the upload of the
+ * prepare before the previous one).  ttc_batch_run then performs, for every pair and level, the same
  * computation as ttc_solve (same results up to rounding; identical for a pair alone
  * or in any batch with the same tile plan).  uint8 pairs of 2..5 levels whose frames
  * and pitch are 16-byte aligned take one launch of the all-levels kernel (every level
