@@ -473,8 +473,10 @@ ft_status ttc_batch_set_plan(ttc_ctx *ctx, const int *rows_per_tile, int levels)
  * two frames' levels 1..L-1; see ttc_pyramid_layout), so each frame is uploaded once
  * and its pyramid built once.  ttc_server_step launches a tick when fewer than two are
  * in flight: at most one waiting frame per stream (oldest arrival first, at most
- * max_batch pairs), uploaded from the caller's host memory on the server's copy stream
- * (one 2-D copy per frame), then one batch on the server's compute stream with the
+ * max_batch pairs), uploaded from the caller's host memory (frames under 1 MB in
+ * page-locked memory whose rows and pitch are whole 16-byte words by one gather kernel
+ * on the server's gather stream that reads that memory directly; the others by one
+ * copy each on the server's copy stream), then one batch on the server's compute stream with the
  * records copied to page-locked host memory; it also reports every frame whose fate is
  * settled.  The multi-scale rule (Sec. V-B) picks each result's level on the host.
  *   ttc_server_create: dtype FT_U8 or FT_F32 frames; levels, mode, rule as elsewhere;
