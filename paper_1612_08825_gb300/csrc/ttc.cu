@@ -998,6 +998,9 @@ __global__ void __launch_bounds__(256) stage_copy_kernel(const StageRanges r)
         const long long w = i - r.start[k];
         r.dst[k][w] = r.src[k][w];
     }
+    // the tensor maps among these words are read by later kernels through the tensor-map
+    // proxy (after their acquire fence): release this thread's generic-proxy stores to it
+    asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
 }
 
 ft_status batch_prepare_impl(ttc_ctx *ctx, const ttc_pair_desc *pairs, int npairs, int dtype, int levels,
